@@ -1,0 +1,174 @@
+/*
+ * libinpaint: exemplar-based object removal on one GB300 GPU (sm_103a).
+ *
+ * The method is the exemplar-based inpainting loop of Sec. 3 of Wang, Xiong,
+ * Yun, Cavallaro, "Computer Vision Accelerators for Mobile Systems based on
+ * OpenCL GPGPU Co-Processing" (J. Sign. Process. Syst., 2014): repeat until
+ * the target region Omega is empty -- compute priorities P(p) = C(p) D(p) on
+ * the fill front (Eq. 1-2), take the highest-priority target patch, find the
+ * source patch with the smallest masked sum of squared RGB differences
+ * (Eq. 3-4, "findBestPatch", 97 % of the run time in Table 2), copy it into
+ * the unknown part of the target patch and update the confidences.
+ *
+ * Every step runs in this library's CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions for all entry points:
+ *   - Images are W x H, row-major, linear index idx(x, y) = y * W + x.
+ *     RGB is 3 interleaved bytes per pixel; rows may be padded (stride).
+ *     A mask byte that is nonzero marks a pixel of Omega (to be removed).
+ *   - The caller owns every host buffer; the library copies inputs when a
+ *     context is created or reset and writes only caller-provided outputs.
+ *   - A return value >= 0 is success, < 0 is an error (inpaint_status).
+ *     No C++ exception crosses this interface.
+ *   - One context is used by one host thread at a time.  Contexts are
+ *     independent; each owns its device memory and uses one CUDA stream.
+ *   - Results are deterministic and bit-identical to the algorithm as stated
+ *     (ties: highest priority, then lowest linear index, is selected; lowest
+ *     SSD, then lowest linear index, is copied).
+ */
+#ifndef INPAINT_H
+#define INPAINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct inpaint_ctx inpaint_ctx; /* opaque; owns its device memory */
+
+typedef enum {
+  INPAINT_OK = 0,
+  INPAINT_DONE = 1,              /* Omega is already empty; nothing was done */
+  INPAINT_ERR_ARG = -1,          /* invalid argument (sizes, radius, pointers, no known pixel) */
+  INPAINT_ERR_NOMEM = -2,        /* a device or pinned-host allocation failed */
+  INPAINT_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+  INPAINT_ERR_NO_SOURCE = -4,    /* no fully-known source patch exists; state unchanged */
+  INPAINT_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+  INPAINT_ERR_UNSUPPORTED = -6,  /* valid request this build or device cannot serve */
+  INPAINT_ERR_INTERNAL = -7      /* a self-check (debug_checks) found inconsistent state */
+} inpaint_status;
+
+/* Search forms (both give identical results). */
+#define INPAINT_FORM_PLAIN 0 /* CUDA-core integer SSD (byte-SIMD abs-diff + dot) */
+#define INPAINT_FORM_TC 1    /* exact tensor-core correlation form (tcgen05, BF16 operands
+                                holding small integers, FP32 accumulation exact below 2^24) */
+
+/* Device allocator hooks: lets a host framework (e.g. PyTorch's caching
+ * allocator) own device memory.  Both NULL: cudaMallocAsync/cudaFreeAsync on
+ * the context's stream.  alloc returns NULL on failure. */
+typedef void* (*inpaint_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*inpaint_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+typedef struct {
+  int form;              /* INPAINT_FORM_PLAIN (default) or INPAINT_FORM_TC */
+  void* cuda_stream;     /* cudaStream_t for all work; NULL = legacy default stream */
+  int debug_checks;      /* nonzero: recount the candidate-validity map from scratch
+                            after every iteration and fail with INPAINT_ERR_INTERNAL
+                            on any difference (slow; for tests) */
+  double search_alpha;   /* < 0: exhaustive search over every interior centre (default).
+                            >= 0: search factor alpha of Sec. 5.3 / Eq. 6: candidate
+                            centres are limited to the bounding box of the initial
+                            Omega expanded by floor(alpha*w) columns left and right and
+                            floor(alpha*h) rows up and down (w x h = box size). */
+  inpaint_alloc_fn dev_alloc;
+  inpaint_free_fn dev_free;
+  void* alloc_user;
+} inpaint_options;
+
+/* One record per fill iteration. */
+typedef struct {
+  int32_t iter;        /* 0-based iteration number */
+  int32_t px, py;      /* target centre p^: highest priority on the fill front */
+  int32_t qx, qy;      /* source centre q~: lowest SSD among valid candidates */
+  uint32_t ssd;        /* SSD of q~ (Eq. 4) over the known pixels of Psi_p^ */
+  double priority;     /* P(p^) = C(p^) * D(p^) (Eq. 1) */
+  double confidence;   /* C(p^) (Eq. 2); the filled pixels receive this value */
+  int32_t filled;      /* pixels of Omega copied this iteration */
+  int32_t remaining;   /* |Omega| after this iteration */
+  int32_t n_known;     /* |K|: known in-image pixels of Psi_p^ */
+  int32_t n_cand;      /* valid candidate centres searched this iteration */
+} inpaint_step_info;
+
+/* Fills *opt with the defaults (plain form, default stream, exhaustive search). */
+void inpaint_options_default(inpaint_options* opt);
+
+/* Creates a context from host RGB + mask and runs the initialisation stage
+ * (Sec. 4.2: grey level, confidence C = 1 on Phi and 0 on Omega, fill front,
+ * priorities, validity map of candidate centres).
+ *   rgb: host, H rows of rgb_stride_bytes (>= 3*W), 3 bytes per pixel.
+ *   mask: host, H rows of mask_stride_bytes (>= W), nonzero = remove.
+ *   patch_radius r: 1..32 (patch side P = 2r+1); W, H >= P.
+ *   opt: NULL for defaults.  *out receives the context.
+ * Errors: INPAINT_ERR_ARG (bad sizes/pointers, mask covering every pixel),
+ * INPAINT_ERR_NOMEM, INPAINT_ERR_CUDA, INPAINT_ERR_UNSUPPORTED (TC form on
+ * a device without tcgen05). On error *out is NULL and nothing leaks. */
+int inpaint_create(const uint8_t* rgb, int width, int height, int rgb_stride_bytes,
+                   const uint8_t* mask, int mask_stride_bytes, int patch_radius,
+                   const inpaint_options* opt, inpaint_ctx** out);
+
+/* Re-initialises an existing context with a new image + mask of the same
+ * size, reusing its device memory.  input_on_device = 0: rgb/mask are host
+ * pointers (copied host->device on the context's stream); 1: device pointers
+ * (densely packed or strided as given), read on the context's stream.
+ * Same errors as inpaint_create. */
+int inpaint_reset(inpaint_ctx* ctx, const uint8_t* rgb, int rgb_stride_bytes,
+                  const uint8_t* mask, int mask_stride_bytes, int input_on_device);
+
+/* One fill iteration (front priorities -> findBestPatch -> copy/update).
+ * Returns INPAINT_OK, INPAINT_DONE (Omega already empty), or an error;
+ * INPAINT_ERR_NO_SOURCE leaves the state unchanged.  info (nullable)
+ * receives the iteration's record.  Synchronises the context's stream. */
+int inpaint_step(inpaint_ctx* ctx, inpaint_step_info* info);
+
+/* Runs iterations on the device until Omega is empty, an error occurs, or
+ * max_iters iterations (<= 0: no limit) have run, with no host round trip
+ * per iteration.  *iters_done (nullable) receives the number of iterations
+ * run by this call; trace (nullable) receives the first min(trace_cap,
+ * iterations) records of this call.  Returns INPAINT_OK when Omega became
+ * empty or max_iters was reached, INPAINT_DONE if Omega was already empty,
+ * or an error. Synchronises the context's stream. */
+int inpaint_run(inpaint_ctx* ctx, int max_iters, int* iters_done,
+                inpaint_step_info* trace, int trace_cap);
+
+/* Copies the current image (RGB, 3 bytes per pixel, rows of stride_bytes)
+ * and optionally the current Omega mask (1 = still unknown, rows of W bytes)
+ * to host memory.  Synchronises the context's stream. */
+int inpaint_result(const inpaint_ctx* ctx, uint8_t* rgb_out, int stride_bytes,
+                   uint8_t* mask_out);
+
+/* Checkpoint of the loop state: image (RGB), Omega (1 byte per pixel) and
+ * confidence C (double per pixel), each dense W x H, any pointer nullable.
+ * With inpaint_import_state it lets a removal stop and resume (the paper's
+ * demo allows iterative editing, Sec. 6). */
+int inpaint_export_state(const inpaint_ctx* ctx, uint8_t* rgb, uint8_t* omega, double* conf);
+
+/* Replaces the loop state of a context by (rgb, omega, conf) from host
+ * memory, as produced by inpaint_export_state, and recomputes everything
+ * derived from it (grey level, front, priorities, validity map).  The
+ * search rectangle of the context is kept. */
+int inpaint_import_state(inpaint_ctx* ctx, const uint8_t* rgb, const uint8_t* omega,
+                         const double* conf);
+
+/* Image geometry and progress. */
+int inpaint_info(const inpaint_ctx* ctx, int* width, int* height, int* patch_radius,
+                 int* remaining, uint64_t* evals);
+
+/* Candidate-centre rectangle [x0,x1] x [y0,y1] the context searches. */
+int inpaint_search_rect(const inpaint_ctx* ctx, int* x0, int* x1, int* y0, int* y1);
+
+/* Releases the context and all its device memory (after synchronising its
+ * stream).  NULL is a no-op. */
+void inpaint_destroy(inpaint_ctx* ctx);
+
+/* Human-readable text for a status code (static storage). */
+const char* inpaint_status_str(int status);
+
+/* Last CUDA error text seen by this thread's most recent failing call. */
+const char* inpaint_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,165 @@
+"""Build and load libinpaint (the CUDA library behind include/inpaint.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no fallback; if the library cannot be built or
+loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import shutil
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+OUT_DIR = os.path.join(PKG, "_build")
+LIB_PATH = os.path.join(OUT_DIR, "libinpaint.so")
+
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+NVCC_FLAGS = [
+    ARCH, "-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",
+    "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC,
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: libinpaint cannot be built")
+
+
+def sources():
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
+def _deps():
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    hdrs += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    return sources() + hdrs + [os.path.abspath(__file__)]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every csrc/*.cu for sm_103a (in parallel) and link libinpaint.so."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _deps())
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+    objs = []
+
+    def compile_one(src):
+        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        p = subprocess.run(cmd, capture_output=True, text=True)
+        if p.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{p.stdout}\n{p.stderr}")
+        if verbose:
+            print(p.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        objs = list(ex.map(compile_one, sources()))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs]
+    p = subprocess.run(cmd, capture_output=True, text=True)
+    if p.returncode != 0:
+        raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [
+        ("iter", ctypes.c_int32), ("px", ctypes.c_int32), ("py", ctypes.c_int32),
+        ("qx", ctypes.c_int32), ("qy", ctypes.c_int32), ("ssd", ctypes.c_uint32),
+        ("priority", ctypes.c_double), ("confidence", ctypes.c_double),
+        ("filled", ctypes.c_int32), ("remaining", ctypes.c_int32),
+        ("n_known", ctypes.c_int32), ("n_cand", ctypes.c_int32),
+    ]
+
+
+STEP_DTYPE = np.dtype(
+    [("iter", np.int32), ("px", np.int32), ("py", np.int32), ("qx", np.int32), ("qy", np.int32),
+     ("ssd", np.uint32), ("priority", np.float64), ("confidence", np.float64),
+     ("filled", np.int32), ("remaining", np.int32), ("n_known", np.int32), ("n_cand", np.int32)],
+    align=True,
+)
+assert STEP_DTYPE.itemsize == ctypes.sizeof(StepInfo)
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("form", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("debug_checks", ctypes.c_int),
+        ("search_alpha", ctypes.c_double), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+        ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+# Exported symbols declared in include/inpaint.h, with their ctypes signatures.
+_P = ctypes.c_void_p
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+_I = ctypes.c_int
+SIGNATURES = {
+    "inpaint_options_default": (None, [ctypes.POINTER(Options)]),
+    "inpaint_create": (_I, [_P, _I, _I, _I, _P, _I, _I, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "inpaint_reset": (_I, [_P, _P, _I, _P, _I, _I]),
+    "inpaint_step": (_I, [_P, ctypes.POINTER(StepInfo)]),
+    "inpaint_run": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int), _P, _I]),
+    "inpaint_result": (_I, [_P, _P, _I, _P]),
+    "inpaint_export_state": (_I, [_P, _P, _P, _P]),
+    "inpaint_import_state": (_I, [_P, _P, _P, _P]),
+    "inpaint_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                          ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_uint64)]),
+    "inpaint_search_rect": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                 ctypes.POINTER(_I)]),
+    "inpaint_destroy": (None, [_P]),
+    "inpaint_status_str": (ctypes.c_char_p, [_I]),
+    "inpaint_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load():
+    """Build if needed and load the library; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class InpaintError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        msg = lib.inpaint_status_str(code).decode()
+        detail = lib.inpaint_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code}){': ' + detail if detail else ''}")
+        self.code = code
+
+
+STATUS = {
+    "OK": 0, "DONE": 1, "ERR_ARG": -1, "ERR_NOMEM": -2, "ERR_CUDA": -3, "ERR_NO_SOURCE": -4,
+    "ERR_TIMEOUT": -5, "ERR_UNSUPPORTED": -6, "ERR_INTERNAL": -7,
+}

@@ -1,0 +1,189 @@
+"""Python binding of libinpaint with the same entry points as include/inpaint.h.
+
+Argument marshalling only.  PyTorch provides the CUDA stream and, through the
+allocator hooks of inpaint_options, the device memory (its caching
+allocator); every step of the method runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import STEP_DTYPE, InpaintError, Options, StepInfo
+
+FORMS = {"plain": 0, "tc": 1}
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("libinpaint needs a CUDA GPU; none is visible")
+    return torch
+
+
+class _TorchAllocator:
+    """inpaint_options.dev_alloc/dev_free backed by PyTorch's caching allocator."""
+
+    def __init__(self, device: int):
+        torch = _torch()
+        self.device = device
+
+        def alloc(nbytes, stream, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+            except Exception:  # noqa: BLE001 - reported to C as NULL (INPAINT_ERR_NOMEM)
+                return None
+
+        def free(ptr, nbytes, stream, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = _lib.ALLOC_FN(alloc)
+        self.free = _lib.FREE_FN(free)
+
+
+def _check(code: int, where: str) -> int:
+    if code < 0:
+        raise InpaintError(code, where)
+    return code
+
+
+def _host_u8(a, shape_tail=()):
+    a = np.ascontiguousarray(a, dtype=np.uint8)
+    return a
+
+
+class Inpainter:
+    """One object-removal job (a context of the C library).
+
+    rgb: (H, W, 3) uint8 array; mask: (H, W), nonzero = remove; r: patch
+    radius (patch side 2r+1).  form: "plain" or "tc".  alpha: search factor
+    of Eq. 6 (negative = exhaustive).  Inputs may be numpy arrays (host) or
+    CUDA torch tensors (device, uint8, contiguous).
+    """
+
+    def __init__(self, rgb, mask, r: int, *, form: str = "plain", alpha: float = -1.0,
+                 debug: bool = False, stream=None, torch_memory: bool = True):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self._alloc = _TorchAllocator(self.device) if torch_memory else None
+        opt = Options()
+        self.lib.inpaint_options_default(ctypes.byref(opt))
+        opt.form = FORMS[form]
+        opt.cuda_stream = self.stream.cuda_stream
+        opt.debug_checks = int(debug)
+        opt.search_alpha = float(alpha)
+        if self._alloc is not None:
+            opt.dev_alloc = self._alloc.alloc
+            opt.dev_free = self._alloc.free
+        self._opt = opt
+        rgb_h = _host_u8(rgb.cpu().numpy() if hasattr(rgb, "cpu") else rgb)
+        mask_h = _host_u8(mask.cpu().numpy() if hasattr(mask, "cpu") else mask)
+        H, W = mask_h.shape
+        assert rgb_h.shape == (H, W, 3)
+        self.W, self.H, self.r = W, H, r
+        ctx = ctypes.c_void_p()
+        _check(self.lib.inpaint_create(rgb_h.ctypes.data, W, H, 3 * W, mask_h.ctypes.data, W, r,
+                                       ctypes.byref(opt), ctypes.byref(ctx)), "inpaint_create")
+        self.ctx = ctx
+
+    # -- lifetime -------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.inpaint_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- loop -----------------------------------------------------------
+    def reset(self, rgb, mask):
+        """New inputs of the same size: numpy (host) or CUDA uint8 tensors (device)."""
+        if hasattr(rgb, "is_cuda") and rgb.is_cuda:
+            assert rgb.is_contiguous() and mask.is_contiguous()
+            return _check(self.lib.inpaint_reset(self.ctx, rgb.data_ptr(), 3 * self.W,
+                                                 mask.data_ptr(), self.W, 1), "inpaint_reset")
+        rgb_h, mask_h = _host_u8(rgb), _host_u8(mask)
+        return _check(self.lib.inpaint_reset(self.ctx, rgb_h.ctypes.data, 3 * self.W,
+                                             mask_h.ctypes.data, self.W, 0), "inpaint_reset")
+
+    def step(self):
+        """One iteration; returns its record (numpy structured scalar) or None when done."""
+        info = StepInfo()
+        rc = _check(self.lib.inpaint_step(self.ctx, ctypes.byref(info)), "inpaint_step")
+        if rc == 1:
+            return None
+        out = np.zeros(1, STEP_DTYPE)
+        ctypes.memmove(out.ctypes.data, ctypes.byref(info), STEP_DTYPE.itemsize)
+        return out[0]
+
+    def run(self, max_iters: int = 0, trace: bool = False, trace_cap: int | None = None):
+        """Iterate on the device; returns (status, iterations, trace array or None)."""
+        done = ctypes.c_int()
+        tr = None
+        ptr, cap = None, 0
+        if trace:
+            cap = trace_cap if trace_cap is not None else self.info()["remaining"] + 1
+            tr = np.zeros(max(cap, 1), STEP_DTYPE)
+            ptr = tr.ctypes.data
+        rc = _check(self.lib.inpaint_run(self.ctx, int(max_iters), ctypes.byref(done), ptr, cap),
+                    "inpaint_run")
+        n = done.value
+        if tr is not None:
+            tr = tr[: min(n, cap)].copy()
+        return rc, n, tr
+
+    def result(self, with_mask: bool = False):
+        rgb = np.zeros((self.H, self.W, 3), np.uint8)
+        m = np.zeros((self.H, self.W), np.uint8) if with_mask else None
+        _check(self.lib.inpaint_result(self.ctx, rgb.ctypes.data, 3 * self.W,
+                                       m.ctypes.data if m is not None else None), "inpaint_result")
+        return (rgb, m) if with_mask else rgb
+
+    def export_state(self):
+        rgb = np.zeros((self.H, self.W, 3), np.uint8)
+        om = np.zeros((self.H, self.W), np.uint8)
+        conf = np.zeros((self.H, self.W), np.float64)
+        _check(self.lib.inpaint_export_state(self.ctx, rgb.ctypes.data, om.ctypes.data,
+                                             conf.ctypes.data), "inpaint_export_state")
+        return rgb, om, conf
+
+    def import_state(self, rgb, omega, conf):
+        rgb = np.ascontiguousarray(rgb, np.uint8)
+        omega = np.ascontiguousarray(omega, np.uint8)
+        conf = np.ascontiguousarray(conf, np.float64)
+        return _check(self.lib.inpaint_import_state(self.ctx, rgb.ctypes.data, omega.ctypes.data,
+                                                    conf.ctypes.data), "inpaint_import_state")
+
+    def info(self):
+        w, h, r, rem = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ev = ctypes.c_uint64()
+        _check(self.lib.inpaint_info(self.ctx, ctypes.byref(w), ctypes.byref(h), ctypes.byref(r),
+                                     ctypes.byref(rem), ctypes.byref(ev)), "inpaint_info")
+        return dict(width=w.value, height=h.value, r=r.value, remaining=rem.value, evals=ev.value)
+
+    def search_rect(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(self.lib.inpaint_search_rect(self.ctx, *[ctypes.byref(x) for x in v]),
+               "inpaint_search_rect")
+        return tuple(x.value for x in v)
+
+
+def remove_object(rgb, mask, r: int, **kw):
+    """Convenience: create, run to completion, return (rgb_out, trace)."""
+    with Inpainter(rgb, mask, r, **kw) as ip:
+        rc, n, tr = ip.run(trace=True)
+        return ip.result(), tr

@@ -1,0 +1,447 @@
+// C-ABI of libinpaint: context lifetime, the iteration loop and host I/O.
+//
+// The three stages of Sec. 4.2 (initialisation, iterative computation,
+// finalisation) map to inpaint_create/inpaint_reset, inpaint_step/inpaint_run
+// and inpaint_result.  inpaint_run drives the whole iterative stage from the
+// device: one CUDA graph whose conditional while-node repeats
+// [findBestPatch search -> copy/update + next selection] until the update
+// kernel reports an empty Omega, so no host round trip happens per iteration.
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "inpaint_internal.cuh"
+
+using namespace inp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  g_last_error = buf;
+  return e == cudaErrorMemoryAllocation ? INPAINT_ERR_NOMEM : INPAINT_ERR_CUDA;
+}
+
+#define CK(call)                                     \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+}  // namespace
+
+struct inpaint_ctx {
+  int W = 0, H = 0, r = 0;
+  inpaint_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ImgState st{};
+  int32_t* sat = nullptr;
+  uint8_t* rgb_stage = nullptr;   // 3*W*H
+  uint8_t* mask_stage = nullptr;  // W*H
+  double* conf_stage = nullptr;   // W*H (import only)
+  Ctrl* h_ctrl = nullptr;         // pinned mirror of the control block
+  int* h_limit = nullptr;         // pinned staging for iter_limit
+  std::vector<std::pair<void*, size_t>> allocs;
+  cudaGraph_t run_graph = nullptr;
+  cudaGraphExec_t run_exec = nullptr;
+  unsigned long long cond = 0;
+
+  void* dalloc(size_t bytes) {
+    void* p = nullptr;
+    if (opt.dev_alloc) {
+      p = opt.dev_alloc(bytes, (void*)stream, opt.alloc_user);
+    } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) allocs.emplace_back(p, bytes);
+    return p;
+  }
+  void release() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (run_exec) cudaGraphExecDestroy(run_exec);
+    if (run_graph) cudaGraphDestroy(run_graph);
+    run_exec = nullptr;
+    run_graph = nullptr;
+    for (auto& a : allocs) {
+      if (opt.dev_free)
+        opt.dev_free(a.first, a.second, (void*)stream, opt.alloc_user);
+      else
+        cudaFreeAsync(a.first, stream);
+    }
+    allocs.clear();
+    if (stream) cudaStreamSynchronize(stream);
+    if (h_ctrl) cudaFreeHost(h_ctrl);
+    if (h_limit) cudaFreeHost(h_limit);
+    h_ctrl = nullptr;
+    h_limit = nullptr;
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+  }
+};
+
+namespace {
+
+template <class T>
+bool alloc_n(inpaint_ctx* c, T*& p, size_t n) {
+  p = static_cast<T*>(c->dalloc(n * sizeof(T)));
+  return p != nullptr;
+}
+
+void search_rect(const uint8_t* mask, int mstride, int W, int H, int r, double alpha,
+                 int* x0o, int* x1o, int* y0o, int* y1o) {
+  int lo_x = r, hi_x = W - 1 - r, lo_y = r, hi_y = H - 1 - r;
+  if (alpha >= 0.0 && mask) {
+    int bx0 = W, bx1 = -1, by0 = H, by1 = -1;
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x)
+        if (mask[(size_t)y * mstride + x]) {
+          bx0 = x < bx0 ? x : bx0;
+          bx1 = x > bx1 ? x : bx1;
+          by0 = y < by0 ? y : by0;
+          by1 = y > by1 ? y : by1;
+        }
+    if (bx1 >= 0) {
+      const int ex = (int)(alpha * (double)(bx1 - bx0 + 1));
+      const int ey = (int)(alpha * (double)(by1 - by0 + 1));
+      lo_x = bx0 - ex > lo_x ? bx0 - ex : lo_x;
+      hi_x = bx1 + ex < hi_x ? bx1 + ex : hi_x;
+      lo_y = by0 - ey > lo_y ? by0 - ey : lo_y;
+      hi_y = by1 + ey < hi_y ? by1 + ey : hi_y;
+    }
+  }
+  *x0o = lo_x;
+  *x1o = hi_x;
+  *y0o = lo_y;
+  *y1o = hi_y;
+}
+
+// Runs the device initialisation from the staging buffers (or device inputs)
+// and checks the outcome.
+int finish_init(inpaint_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_ctrl, c->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->h_ctrl->remaining == c->W * c->H) {
+    g_last_error = "mask covers every pixel: no known pixel to copy from";
+    return INPAINT_ERR_ARG;
+  }
+  if (c->h_ctrl->status != 0) return c->h_ctrl->status;
+  return INPAINT_OK;
+}
+
+int check_geometry(int W, int H, int r) {
+  if (r < 1 || r > kMaxRadius) {
+    g_last_error = "patch radius must be in 1..32";
+    return INPAINT_ERR_ARG;
+  }
+  if (W < 2 * r + 1 || H < 2 * r + 1 || (long long)W * H > (1ll << 30)) {
+    g_last_error = "image must be at least (2r+1) x (2r+1) and below 2^30 pixels";
+    return INPAINT_ERR_ARG;
+  }
+  return INPAINT_OK;
+}
+
+int launch_iteration(inpaint_ctx* c, int use_cond) {
+  CK(launch_search_plain(c->st, c->stream));
+  CK(launch_update(c->st, 1, c->cond, use_cond, c->stream));
+  if (c->opt.debug_checks) CK(launch_verify_count(c->st, c->stream));
+  return INPAINT_OK;
+}
+
+int build_run_graph(inpaint_ctx* c) {
+  if (c->run_exec) return INPAINT_OK;
+  CK(cudaGraphCreate(&c->run_graph, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, c->run_graph, 1, cudaGraphCondAssignDefault));
+  c->cond = (unsigned long long)h;
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, c->run_graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  int rc = launch_iteration(c, 1);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &captured);
+  if (rc != INPAINT_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  CK(cudaGraphInstantiate(&c->run_exec, c->run_graph, 0));
+  return INPAINT_OK;
+}
+
+int set_limit(inpaint_ctx* c, int limit) {
+  *c->h_limit = limit;
+  CK(cudaMemcpyAsync(&c->st.ctrl->iter_limit, c->h_limit, sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream));
+  return INPAINT_OK;
+}
+
+int read_ctrl(const inpaint_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_ctrl, c->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return INPAINT_OK;
+}
+
+int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t* mask,
+                int mask_stride, int r, const inpaint_options* opt, inpaint_ctx** out) {
+  if (!out) return INPAINT_ERR_ARG;
+  *out = nullptr;
+  if (!rgb || !mask || rgb_stride < 3 * W || mask_stride < W) {
+    g_last_error = "null input or stride smaller than a row";
+    return INPAINT_ERR_ARG;
+  }
+  int rc = check_geometry(W, H, r);
+  if (rc) return rc;
+  inpaint_options o;
+  inpaint_options_default(&o);
+  if (opt) o = *opt;
+  if (o.form != INPAINT_FORM_PLAIN && o.form != INPAINT_FORM_TC) return INPAINT_ERR_ARG;
+  if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr)) {
+    g_last_error = "dev_alloc and dev_free must be given together";
+    return INPAINT_ERR_ARG;
+  }
+  if (o.form == INPAINT_FORM_TC) {
+    g_last_error = "tensor-core form not built yet";
+    return INPAINT_ERR_UNSUPPORTED;
+  }
+
+  inpaint_ctx* c = new (std::nothrow) inpaint_ctx();
+  if (!c) return INPAINT_ERR_NOMEM;
+  c->W = W;
+  c->H = H;
+  c->r = r;
+  c->opt = o;
+  auto fail = [&](int code) {
+    c->release();
+    delete c;
+    return code;
+  };
+  if (o.cuda_stream) {
+    c->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(INPAINT_ERR_CUDA);
+    c->own_stream = true;
+  }
+  if (cudaMallocHost(&c->h_ctrl, sizeof(Ctrl)) != cudaSuccess) return fail(INPAINT_ERR_NOMEM);
+  if (cudaMallocHost(&c->h_limit, sizeof(int)) != cudaSuccess) return fail(INPAINT_ERR_NOMEM);
+
+  ImgState& s = c->st;
+  s.W = W;
+  s.H = H;
+  s.r = r;
+  search_rect(mask, mask_stride, W, H, r, o.search_alpha, &s.cx0, &s.cx1, &s.cy0, &s.cy1);
+  s.tiles_x = (W + kPrioTile - 1) / kPrioTile;
+  s.tiles_y = (H + kPrioTile - 1) / kPrioTile;
+  size_t n_omega = 0;
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) n_omega += mask[(size_t)y * mask_stride + x] != 0;
+  s.trace_cap = (int)n_omega + 1;
+  const dim3 g = search_plain_grid(s);
+  s.n_partial = (int)(g.x * g.y);
+  const size_t n = (size_t)W * H;
+  if (!alloc_n(c, s.img, n) || !alloc_n(c, s.omega, n) || !alloc_n(c, s.gray, n) ||
+      !alloc_n(c, s.conf, n) || !alloc_n(c, s.count, n) || !alloc_n(c, s.prio, n) ||
+      !alloc_n(c, s.pconf, n) || !alloc_n(c, s.tiles, (size_t)s.tiles_x * s.tiles_y) ||
+      !alloc_n(c, s.ctrl, 1) || !alloc_n(c, s.trace, (size_t)s.trace_cap) ||
+      !alloc_n(c, s.partial, (size_t)(s.n_partial > 0 ? s.n_partial : 1)) ||
+      !alloc_n(c, c->sat, (size_t)(W + 1) * (H + 1)) || !alloc_n(c, c->rgb_stage, 3 * n) ||
+      !alloc_n(c, c->mask_stage, n)) {
+    g_last_error = "device allocation failed";
+    return fail(INPAINT_ERR_NOMEM);
+  }
+  if (prepare_search_plain(r) != cudaSuccess) return fail(INPAINT_ERR_CUDA);
+  *out = c;
+  rc = inpaint_reset(c, rgb, rgb_stride, mask, mask_stride, 0);
+  if (rc < 0) {
+    *out = nullptr;
+    return fail(rc);
+  }
+  return INPAINT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void inpaint_options_default(inpaint_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof *opt);
+  opt->form = INPAINT_FORM_PLAIN;
+  opt->search_alpha = -1.0;
+}
+
+int inpaint_create(const uint8_t* rgb, int width, int height, int rgb_stride_bytes,
+                   const uint8_t* mask, int mask_stride_bytes, int patch_radius,
+                   const inpaint_options* opt, inpaint_ctx** out) {
+  try {
+    return create_impl(rgb, width, height, rgb_stride_bytes, mask, mask_stride_bytes,
+                       patch_radius, opt, out);
+  } catch (...) {
+    return INPAINT_ERR_NOMEM;
+  }
+}
+
+int inpaint_reset(inpaint_ctx* c, const uint8_t* rgb, int rgb_stride, const uint8_t* mask,
+                  int mask_stride, int input_on_device) {
+  if (!c || !rgb || !mask || rgb_stride < 3 * c->W || mask_stride < c->W) return INPAINT_ERR_ARG;
+  const int W = c->W, H = c->H;
+  const uint8_t* drgb = rgb;
+  const uint8_t* dmask = mask;
+  int rs = rgb_stride, ms = mask_stride;
+  if (!input_on_device) {
+    CK(cudaMemcpy2DAsync(c->rgb_stage, 3 * (size_t)W, rgb, rgb_stride, 3 * (size_t)W, H,
+                         cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpy2DAsync(c->mask_stage, W, mask, mask_stride, W, H, cudaMemcpyHostToDevice,
+                         c->stream));
+    drgb = c->rgb_stage;
+    dmask = c->mask_stage;
+    rs = 3 * W;
+    ms = W;
+  }
+  CK(launch_init(c->st, drgb, rs, dmask, ms, c->sat, nullptr, c->stream));
+  return finish_init(c);
+}
+
+int inpaint_step(inpaint_ctx* c, inpaint_step_info* info) {
+  if (!c) return INPAINT_ERR_ARG;
+  int rc = read_ctrl(c);
+  if (rc) return rc;
+  if (c->h_ctrl->status != 0) return c->h_ctrl->status;
+  if (c->h_ctrl->remaining == 0) return INPAINT_DONE;
+  if ((rc = set_limit(c, INT_MAX))) return rc;
+  if ((rc = launch_iteration(c, 0))) return rc;
+  if ((rc = read_ctrl(c))) return rc;
+  if (c->h_ctrl->status != 0) return c->h_ctrl->status;
+  if (info) *info = c->h_ctrl->last;
+  return INPAINT_OK;
+}
+
+int inpaint_run(inpaint_ctx* c, int max_iters, int* iters_done, inpaint_step_info* trace,
+                int trace_cap) {
+  if (iters_done) *iters_done = 0;
+  if (!c || (trace && trace_cap < 0)) return INPAINT_ERR_ARG;
+  int rc = read_ctrl(c);
+  if (rc) return rc;
+  if (c->h_ctrl->status != 0) return c->h_ctrl->status;
+  if (c->h_ctrl->remaining == 0) return INPAINT_DONE;
+  const int start = c->h_ctrl->iter;
+  // Every iteration fills at least one pixel, so |Omega| iterations always
+  // suffice: the device loop is bounded even if a kernel misbehaved.
+  long long lim = (long long)start + c->h_ctrl->remaining;
+  if (max_iters > 0 && (long long)start + max_iters < lim) lim = (long long)start + max_iters;
+  if ((rc = build_run_graph(c))) return rc;
+  if ((rc = set_limit(c, lim > INT_MAX ? INT_MAX : (int)lim))) return rc;
+  CK(cudaGraphLaunch(c->run_exec, c->stream));
+  if ((rc = set_limit(c, INT_MAX))) return rc;
+  if ((rc = read_ctrl(c))) return rc;
+  const int done = c->h_ctrl->iter - start;
+  if (iters_done) *iters_done = done;
+  if (trace && trace_cap > 0 && done > 0) {
+    int n = done < trace_cap ? done : trace_cap;
+    if (start + n > c->st.trace_cap) n = c->st.trace_cap - start;
+    if (n > 0) {
+      CK(cudaMemcpyAsync(trace, c->st.trace + start, (size_t)n * sizeof(inpaint_step_info),
+                         cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+  }
+  if (c->h_ctrl->status != 0) return c->h_ctrl->status;
+  return INPAINT_OK;
+}
+
+int inpaint_result(const inpaint_ctx* c, uint8_t* rgb_out, int stride, uint8_t* mask_out) {
+  if (!c || !rgb_out || stride < 3 * c->W) return INPAINT_ERR_ARG;
+  CK(launch_export(c->st, c->rgb_stage, c->stream));
+  CK(cudaMemcpy2DAsync(rgb_out, stride, c->rgb_stage, 3 * (size_t)c->W, 3 * (size_t)c->W, c->H,
+                       cudaMemcpyDeviceToHost, c->stream));
+  if (mask_out)
+    CK(cudaMemcpyAsync(mask_out, c->st.omega, (size_t)c->W * c->H, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return INPAINT_OK;
+}
+
+int inpaint_export_state(const inpaint_ctx* c, uint8_t* rgb, uint8_t* omega, double* conf) {
+  if (!c) return INPAINT_ERR_ARG;
+  const size_t n = (size_t)c->W * c->H;
+  if (rgb) {
+    CK(launch_export(c->st, c->rgb_stage, c->stream));
+    CK(cudaMemcpyAsync(rgb, c->rgb_stage, 3 * n, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (omega) CK(cudaMemcpyAsync(omega, c->st.omega, n, cudaMemcpyDeviceToHost, c->stream));
+  if (conf)
+    CK(cudaMemcpyAsync(conf, c->st.conf, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return INPAINT_OK;
+}
+
+int inpaint_import_state(inpaint_ctx* c, const uint8_t* rgb, const uint8_t* omega,
+                         const double* conf) {
+  if (!c || !rgb || !omega || !conf) return INPAINT_ERR_ARG;
+  const size_t n = (size_t)c->W * c->H;
+  if (!c->conf_stage && !alloc_n(c, c->conf_stage, n)) return INPAINT_ERR_NOMEM;
+  CK(cudaMemcpyAsync(c->rgb_stage, rgb, 3 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->mask_stage, omega, n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->conf_stage, conf, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(launch_import(c->st, c->rgb_stage, c->mask_stage, c->conf_stage, c->sat, nullptr,
+                   c->stream));
+  return finish_init(c);
+}
+
+int inpaint_info(const inpaint_ctx* c, int* width, int* height, int* patch_radius, int* remaining,
+                 uint64_t* evals) {
+  if (!c) return INPAINT_ERR_ARG;
+  int rc = read_ctrl(c);
+  if (rc) return rc;
+  if (width) *width = c->W;
+  if (height) *height = c->H;
+  if (patch_radius) *patch_radius = c->r;
+  if (remaining) *remaining = c->h_ctrl->remaining;
+  if (evals) *evals = c->h_ctrl->evals;
+  return INPAINT_OK;
+}
+
+int inpaint_search_rect(const inpaint_ctx* c, int* x0, int* x1, int* y0, int* y1) {
+  if (!c) return INPAINT_ERR_ARG;
+  if (x0) *x0 = c->st.cx0;
+  if (x1) *x1 = c->st.cx1;
+  if (y0) *y0 = c->st.cy0;
+  if (y1) *y1 = c->st.cy1;
+  return INPAINT_OK;
+}
+
+void inpaint_destroy(inpaint_ctx* c) {
+  if (!c) return;
+  c->release();
+  delete c;
+}
+
+const char* inpaint_status_str(int s) {
+  switch (s) {
+    case INPAINT_OK: return "ok";
+    case INPAINT_DONE: return "done: target region already empty";
+    case INPAINT_ERR_ARG: return "invalid argument";
+    case INPAINT_ERR_NOMEM: return "out of memory";
+    case INPAINT_ERR_CUDA: return "CUDA error";
+    case INPAINT_ERR_NO_SOURCE: return "no fully-known source patch";
+    case INPAINT_ERR_TIMEOUT: return "device wait timed out";
+    case INPAINT_ERR_UNSUPPORTED: return "unsupported";
+    case INPAINT_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+const char* inpaint_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

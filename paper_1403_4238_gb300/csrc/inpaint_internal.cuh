@@ -1,0 +1,193 @@
+// Device-side state and helpers shared by the kernels of libinpaint.
+//
+// Data layout in HBM for one image of W x H pixels (patch radius r):
+//   img    uint32[W*H]   RGBA8 (R in the low byte, A = 0): one pixel per word,
+//                        so a pixel is one 32-bit load and byte-SIMD works on it
+//   omega  uint8[W*H]    1 = pixel of the target region Omega (still unknown)
+//   gray   uint8[W*H]    integer luma of known pixels (0 under Omega)
+//   conf   double[W*H]   confidence C (Eq. 2), 0 under Omega
+//   count  int32[W*H]    for a candidate centre q: unknown pixels in Psi_q
+//                        (valid source patch iff 0); borders hold a large value
+//   prio   uint64[W*H]   priority key of a front pixel: bits(P(p)) + 1; 0 off
+//                        the front (P >= 0, so the bits order like the values)
+//   pconf  double[W*H]   C(p) of the last priority evaluation at p
+//   tiles  PrioBest[]    best (key, idx) per 32x32 tile of prio: the argmax
+//                        over the front touches only tiles, not pixels
+//   ctrl   Ctrl          loop control block (selected p^, counters, status)
+//   trace  inpaint_step_info[trace_cap]   one record per iteration
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "inpaint.h"
+
+namespace inp {
+
+constexpr int kPrioTile = 32;   // edge of a priority tile
+constexpr int kMaxRadius = 32;  // largest supported patch radius
+constexpr int kCountInvalid = 1 << 28;  // count of a centre whose patch leaves the image
+
+// Plain search tile: 8 candidate rows x 128 candidate columns per CTA, each
+// thread computes 4 horizontally adjacent candidates.
+constexpr int kSearchTW = 128;
+constexpr int kSearchTH = 8;
+constexpr int kSearchS = 4;
+constexpr int kSearchThreads = (kSearchTW / kSearchS) * kSearchTH;  // 256
+// Generic (large-radius) search tile.
+constexpr int kGenTW = 64;
+constexpr int kGenTH = 8;
+constexpr int kGenS = 2;
+constexpr int kGenThreads = (kGenTW / kGenS) * kGenTH;  // 256
+
+constexpr int kUpdThreads = 512;
+
+struct PrioBest {
+  unsigned long long key;
+  int idx;
+  int pad;
+};
+
+struct Ctrl {
+  int iter;        // iterations completed
+  int remaining;   // |Omega|
+  int status;      // 0 = running, else an inpaint_status error
+  int px, py;      // target centre selected for the next iteration (-1: none)
+  int n_valid;     // valid candidate centres inside the search rectangle
+  int iter_limit;  // kernels do nothing once iter reaches this
+  int pad0;
+  double prio;     // P(p^) of the selected target
+  double conf;     // C(p^) of the selected target
+  unsigned long long evals;  // sum over iterations of n_cand * n_known
+  inpaint_step_info last;    // record of the most recent iteration
+};
+
+struct ImgState {
+  int W, H, r;
+  int cx0, cx1, cy0, cy1;  // candidate-centre rectangle (inclusive)
+  int tiles_x, tiles_y;
+  int trace_cap;
+  int n_partial;           // search CTAs writing partial[]
+  uint32_t* img;
+  uint8_t* omega;
+  uint8_t* gray;
+  double* conf;
+  int32_t* count;
+  unsigned long long* prio;
+  double* pconf;
+  PrioBest* tiles;
+  Ctrl* ctrl;
+  inpaint_step_info* trace;
+  unsigned long long* partial;  // per-CTA best search key of the iteration
+};
+
+__host__ __device__ inline uint32_t pack_rgb(uint32_t r, uint32_t g, uint32_t b) {
+  return r | (g << 8) | (b << 16);
+}
+
+__host__ __device__ inline uint32_t luma_word(uint32_t w) {
+  uint32_t r = w & 255u, g = (w >> 8) & 255u, b = (w >> 16) & 255u;
+  return (299u * r + 587u * g + 114u * b + 500u) / 1000u;
+}
+
+// Loop is still running (uniform across a CTA: everyone reads the same word).
+__device__ inline bool loop_active(const Ctrl* c) {
+  return c->status == 0 && c->remaining > 0 && c->iter < c->iter_limit;
+}
+
+// Priority argmax order: larger key first, then lower index.
+__device__ inline bool prio_better(unsigned long long ka, int ia, unsigned long long kb, int ib) {
+  return ka > kb || (ka == kb && ia < ib);
+}
+
+__device__ inline unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t < v ? t : v;
+  }
+  return v;
+}
+
+__device__ inline void warp_best_prio(unsigned long long& k, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long tk = __shfl_xor_sync(0xffffffffu, k, o);
+    int ti = __shfl_xor_sync(0xffffffffu, i, o);
+    if (prio_better(tk, ti, k, i)) {
+      k = tk;
+      i = ti;
+    }
+  }
+}
+
+// Block-wide best (key, idx); every thread gets the result.  scratch holds
+// one entry per warp; blockDim.x must be a multiple of 32.
+__device__ inline void block_best_prio(unsigned long long& k, int& i, PrioBest* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  warp_best_prio(k, i);
+  __syncthreads();
+  if (lane == 0) {
+    scratch[wid].key = k;
+    scratch[wid].idx = i;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long kk = lane < nw ? scratch[lane].key : 0ull;
+    int ii = lane < nw ? scratch[lane].idx : 0x7fffffff;
+    warp_best_prio(kk, ii);
+    if (lane == 0) {
+      scratch[0].key = kk;
+      scratch[0].idx = ii;
+    }
+  }
+  __syncthreads();
+  k = scratch[0].key;
+  i = scratch[0].idx;
+}
+
+__device__ inline unsigned long long block_min_u64(unsigned long long v, unsigned long long* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_min_u64(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long t = lane < nw ? scratch[lane] : ~0ull;
+    t = warp_min_u64(t);
+    if (lane == 0) scratch[0] = t;
+  }
+  __syncthreads();
+  return scratch[0];
+}
+
+__device__ inline int block_sum_int(int v, int* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int t = lane < nw ? scratch[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) scratch[0] = t;
+  }
+  __syncthreads();
+  return scratch[0];
+}
+
+// ---- host-side launchers (defined in the .cu files) ----
+cudaError_t launch_init(const ImgState& s, const uint8_t* rgb, int rgb_stride, const uint8_t* mask,
+                        int mask_stride, int32_t* sat, int* omega_count, cudaStream_t st);
+cudaError_t launch_import(const ImgState& s, const uint8_t* rgb, const uint8_t* omega,
+                          const double* conf, int32_t* sat, int* omega_count, cudaStream_t st);
+cudaError_t prepare_search_plain(int r);
+cudaError_t launch_search_plain(const ImgState& s, cudaStream_t st);
+dim3 search_plain_grid(const ImgState& s);
+cudaError_t launch_update(const ImgState& s, int do_fill, unsigned long long cond_handle,
+                          int use_cond, cudaStream_t st);
+cudaError_t launch_verify_count(const ImgState& s, cudaStream_t st);
+cudaError_t launch_export(const ImgState& s, uint8_t* rgb_dense, cudaStream_t st);
+
+}  // namespace inp
