@@ -63,7 +63,8 @@ typedef void (*inpaint_free_fn)(void* ptr, size_t bytes, void* stream, void* use
 
 typedef struct {
   int form;              /* INPAINT_FORM_PLAIN (default) or INPAINT_FORM_TC */
-  void* cuda_stream;     /* cudaStream_t for all work; NULL = legacy default stream */
+  void* cuda_stream;     /* cudaStream_t for all work; NULL = a non-blocking stream the
+                            context creates and owns */
   int debug_checks;      /* nonzero: recount the candidate-validity map from scratch
                             after every iteration and fail with INPAINT_ERR_INTERNAL
                             on any difference (slow; for tests) */
@@ -75,7 +76,20 @@ typedef struct {
   inpaint_alloc_fn dev_alloc;
   inpaint_free_fn dev_free;
   void* alloc_user;
+  int loop_mode;         /* how inpaint_run drives the iterations:
+                            INPAINT_LOOP_AUTO (default): the persistent engine when
+                            patch_radius <= 8, else the graph loop;
+                            INPAINT_LOOP_ENGINE: one cooperative persistent kernel for
+                            the whole loop (patch_radius <= 8 only);
+                            INPAINT_LOOP_GRAPH: a CUDA graph with a conditional while
+                            node around [search kernel, update kernel] */
+  int tile_rows;         /* engine search unit height in candidate rows: 1, 2 or 4;
+                            0 = chosen by the library (autotuned table) */
 } inpaint_options;
+
+#define INPAINT_LOOP_AUTO 0
+#define INPAINT_LOOP_ENGINE 1
+#define INPAINT_LOOP_GRAPH 2
 
 /* One record per fill iteration. */
 typedef struct {
@@ -154,6 +168,15 @@ int inpaint_import_state(inpaint_ctx* ctx, const uint8_t* rgb, const uint8_t* om
 /* Image geometry and progress. */
 int inpaint_info(const inpaint_ctx* ctx, int* width, int* height, int* patch_radius,
                  int* remaining, uint64_t* evals);
+
+/* Phase clocks of the persistent engine since the last create/reset, from
+ * the GPU's global timer: *search_ns sums, per iteration, the time from the
+ * publication of the previous iteration to the last search CTA's arrival
+ * (target staging, findBestPatch over all candidates, reduction, arrival);
+ * *update_ns sums the copy/update/selection phases; *iters counts the
+ * iterations timed.  The graph loop is not timed (all zero). */
+int inpaint_loop_timing(const inpaint_ctx* ctx, uint64_t* search_ns, uint64_t* update_ns,
+                        int* iters);
 
 /* Candidate-centre rectangle [x0,x1] x [y0,y1] the context searches. */
 int inpaint_search_rect(const inpaint_ctx* ctx, int* x0, int* x1, int* y0, int* y1);

@@ -91,6 +91,12 @@ class StepInfo(ctypes.Structure):
     ]
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("ssd_evals_per_s", ctypes.c_double), ("imad_per_s", ctypes.c_double),
+                ("iadd3_per_s", ctypes.c_double), ("dadd_per_s", ctypes.c_double),
+                ("sm_clock_mhz", ctypes.c_double), ("sm_count", ctypes.c_int)]
+
+
 STEP_DTYPE = np.dtype(
     [("iter", np.int32), ("px", np.int32), ("py", np.int32), ("qx", np.int32), ("qy", np.int32),
      ("ssd", np.uint32), ("priority", np.float64), ("confidence", np.float64),
@@ -107,7 +113,7 @@ class Options(ctypes.Structure):
     _fields_ = [
         ("form", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("debug_checks", ctypes.c_int),
         ("search_alpha", ctypes.c_double), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-        ("alloc_user", ctypes.c_void_p),
+        ("alloc_user", ctypes.c_void_p), ("loop_mode", ctypes.c_int), ("tile_rows", ctypes.c_int),
     ]
 
 
@@ -131,6 +137,9 @@ SIGNATURES = {
     "inpaint_destroy": (None, [_P]),
     "inpaint_status_str": (ctypes.c_char_p, [_I]),
     "inpaint_last_error": (ctypes.c_char_p, []),
+    "inpaint_probe_peaks": (_I, [ctypes.POINTER(Peaks)]),
+    "inpaint_loop_timing": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(_I)]),
 }
 
 

@@ -14,6 +14,7 @@ from . import _lib
 from ._lib import STEP_DTYPE, InpaintError, Options, StepInfo
 
 FORMS = {"plain": 0, "tc": 1}
+LOOPS = {"auto": 0, "engine": 1, "graph": 2}
 
 
 def _torch():
@@ -60,12 +61,15 @@ class Inpainter:
 
     rgb: (H, W, 3) uint8 array; mask: (H, W), nonzero = remove; r: patch
     radius (patch side 2r+1).  form: "plain" or "tc".  alpha: search factor
-    of Eq. 6 (negative = exhaustive).  Inputs may be numpy arrays (host) or
+    of Eq. 6 (negative = exhaustive).  loop: "auto", "engine" (persistent
+    kernel) or "graph" (conditional CUDA graph).  tile_rows: engine search
+    unit height (0 = library choice).  Inputs may be numpy arrays (host) or
     CUDA torch tensors (device, uint8, contiguous).
     """
 
     def __init__(self, rgb, mask, r: int, *, form: str = "plain", alpha: float = -1.0,
-                 debug: bool = False, stream=None, torch_memory: bool = True):
+                 debug: bool = False, stream=None, torch_memory: bool = True,
+                 loop: str = "auto", tile_rows: int = 0):
         torch = _torch()
         self.lib = _lib.load()
         self.device = torch.cuda.current_device()
@@ -77,6 +81,8 @@ class Inpainter:
         opt.cuda_stream = self.stream.cuda_stream
         opt.debug_checks = int(debug)
         opt.search_alpha = float(alpha)
+        opt.loop_mode = LOOPS[loop]
+        opt.tile_rows = int(tile_rows)
         if self._alloc is not None:
             opt.dev_alloc = self._alloc.alloc
             opt.dev_free = self._alloc.free
@@ -175,6 +181,13 @@ class Inpainter:
                                      ctypes.byref(rem), ctypes.byref(ev)), "inpaint_info")
         return dict(width=w.value, height=h.value, r=r.value, remaining=rem.value, evals=ev.value)
 
+    def loop_timing(self):
+        """Engine phase clocks since create/reset: (search_ns, update_ns, iterations)."""
+        a, b, n = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+        _check(self.lib.inpaint_loop_timing(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+               "inpaint_loop_timing")
+        return a.value, b.value, n.value
+
     def search_rect(self):
         v = [ctypes.c_int() for _ in range(4)]
         _check(self.lib.inpaint_search_rect(self.ctx, *[ctypes.byref(x) for x in v]),
@@ -187,3 +200,12 @@ def remove_object(rgb, mask, r: int, **kw):
     with Inpainter(rgb, mask, r, **kw) as ip:
         rc, n, tr = ip.run(trace=True)
         return ip.result(), tr
+
+
+def probe_peaks() -> dict:
+    """Measured instruction-rate peaks of the current GPU (inpaint_probe_peaks)."""
+    _torch()
+    lib = _lib.load()
+    pk = _lib.Peaks()
+    _check(lib.inpaint_probe_peaks(ctypes.byref(pk)), "inpaint_probe_peaks")
+    return {f: getattr(pk, f) for f, _ in _lib.Peaks._fields_}

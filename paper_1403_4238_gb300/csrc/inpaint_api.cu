@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "inpaint_engine.h"
 #include "inpaint_internal.cuh"
 
 using namespace inp;
@@ -52,6 +53,17 @@ struct inpaint_ctx {
   cudaGraph_t run_graph = nullptr;
   cudaGraphExec_t run_exec = nullptr;
   unsigned long long cond = 0;
+  // persistent engine (one team of every CTA)
+  bool eng_ready = false;
+  int eng_grid = 0, eng_sr = 0;
+  EngineArgs ea{};
+  ImgState* d_img = nullptr;
+  CUtensorMap* d_tmap = nullptr;
+  int* d_ints = nullptr;     // cta_team[grid], team_first[2], team_img_off[2], team_img[1]
+  TeamCtl* d_team = nullptr;
+  unsigned long long* d_epart = nullptr;
+  int* d_err = nullptr;
+  int* h_err = nullptr;
 
   void* dalloc(size_t bytes) {
     void* p = nullptr;
@@ -79,8 +91,10 @@ struct inpaint_ctx {
     if (stream) cudaStreamSynchronize(stream);
     if (h_ctrl) cudaFreeHost(h_ctrl);
     if (h_limit) cudaFreeHost(h_limit);
+    if (h_err) cudaFreeHost(h_err);
     h_ctrl = nullptr;
     h_limit = nullptr;
+    h_err = nullptr;
     if (own_stream && stream) cudaStreamDestroy(stream);
     stream = nullptr;
   }
@@ -149,8 +163,94 @@ int check_geometry(int W, int H, int r) {
 
 int launch_iteration(inpaint_ctx* c, int use_cond) {
   CK(launch_search_plain(c->st, c->stream));
-  CK(launch_update(c->st, 1, c->cond, use_cond, c->stream));
+  if (c->r <= 8)
+    CK(launch_update_fast(c->st, c->cond, use_cond, c->stream));
+  else
+    CK(launch_update(c->st, 1, c->cond, use_cond, c->stream));
   if (c->opt.debug_checks) CK(launch_verify_count(c->st, c->stream));
+  return INPAINT_OK;
+}
+
+bool use_engine(const inpaint_ctx* c) {
+  if (c->opt.loop_mode == INPAINT_LOOP_GRAPH) return false;
+  return c->r <= 8;
+}
+
+// Search unit height: the tallest (best reuse of staged rows) that still
+// gives every warp of the grid about two units.
+int pick_tile_rows(const ImgState& s, int grid_warps) {
+  const int xb = s.r + ((s.cx0 - s.r) & ~3);
+  const long long ncg = (s.cx1 - xb + 128) / 128, ch = s.cy1 - s.cy0 + 1;
+  for (int sr = 4; sr > 1; sr >>= 1)
+    if (ncg * ((ch + sr - 1) / sr) >= 2ll * grid_warps) return sr;
+  return 1;
+}
+
+int setup_engine(inpaint_ctx* c) {
+  if (c->eng_ready) return INPAINT_OK;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int sr = c->opt.tile_rows;
+  if (sr != 0 && sr != 1 && sr != 2 && sr != 4) {
+    g_last_error = "tile_rows must be 0, 1, 2 or 4";
+    return INPAINT_ERR_ARG;
+  }
+  int bps = 0;
+  CK(engine_occupancy(c->r, sr ? sr : 4, &bps));
+  if (bps < 1) {
+    g_last_error = "engine kernel does not fit on an SM";
+    return INPAINT_ERR_UNSUPPORTED;
+  }
+  const int grid = sms * bps;
+  if (!sr) sr = pick_tile_rows(c->st, grid * kEngWarps);
+  CK(engine_occupancy(c->r, sr, &bps));
+  const int g2 = sms * (bps < 1 ? 1 : bps);
+  c->eng_grid = g2 < grid ? g2 : grid;
+  c->eng_sr = sr;
+  if (!alloc_n(c, c->d_img, 1) || !alloc_n(c, c->d_tmap, 1) ||
+      !alloc_n(c, c->d_ints, (size_t)c->eng_grid + 5) || !alloc_n(c, c->d_team, 1) ||
+      !alloc_n(c, c->d_epart, (size_t)c->eng_grid) || !alloc_n(c, c->d_err, 1))
+    return INPAINT_ERR_NOMEM;
+  if (!c->h_err && cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) return INPAINT_ERR_NOMEM;
+  CUtensorMap tm;
+  if (make_image_tmap(c->st, sr, &tm) != 0) {
+    g_last_error = "cuTensorMapEncodeTiled failed";
+    return INPAINT_ERR_CUDA;
+  }
+  std::vector<int> ints((size_t)c->eng_grid + 5, 0);  // every CTA in team 0
+  ints[c->eng_grid + 0] = 0;
+  ints[c->eng_grid + 1] = c->eng_grid;  // team_first = {0, grid}
+  ints[c->eng_grid + 2] = 0;
+  ints[c->eng_grid + 3] = 1;            // team_img_off = {0, 1}
+  ints[c->eng_grid + 4] = 0;            // team_img = {0}
+  CK(cudaMemcpyAsync(c->d_img, &c->st, sizeof(ImgState), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_tmap, &tm, sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  EngineArgs& ea = c->ea;
+  ea.imgs = c->d_img;
+  ea.tmaps = c->d_tmap;
+  ea.cta_team = c->d_ints;
+  ea.team_first = c->d_ints + c->eng_grid;
+  ea.team_img_off = c->d_ints + c->eng_grid + 2;
+  ea.team_img = c->d_ints + c->eng_grid + 4;
+  ea.teams = c->d_team;
+  ea.partials = c->d_epart;
+  ea.err = c->d_err;
+  ea.wait_limit_ns = 4000000000ull;  // 4 s: far beyond any iteration
+  c->eng_ready = true;
+  return INPAINT_OK;
+}
+
+int run_engine(inpaint_ctx* c) {
+  int rc = setup_engine(c);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(c->d_team, 0, sizeof(TeamCtl), c->stream));
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CK(engine_launch(c->r, c->eng_sr, c->ea, c->eng_grid, c->stream));
+  CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   return INPAINT_OK;
 }
 
@@ -206,6 +306,11 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
   inpaint_options_default(&o);
   if (opt) o = *opt;
   if (o.form != INPAINT_FORM_PLAIN && o.form != INPAINT_FORM_TC) return INPAINT_ERR_ARG;
+  if (o.loop_mode < INPAINT_LOOP_AUTO || o.loop_mode > INPAINT_LOOP_GRAPH) return INPAINT_ERR_ARG;
+  if (o.loop_mode == INPAINT_LOOP_ENGINE && r > 8) {
+    g_last_error = "the persistent engine supports patch_radius <= 8";
+    return INPAINT_ERR_UNSUPPORTED;
+  }
   if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr)) {
     g_last_error = "dev_alloc and dev_free must be given together";
     return INPAINT_ERR_ARG;
@@ -241,8 +346,11 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
   s.H = H;
   s.r = r;
   search_rect(mask, mask_stride, W, H, r, o.search_alpha, &s.cx0, &s.cx1, &s.cy0, &s.cy1);
-  s.tiles_x = (W + kPrioTile - 1) / kPrioTile;
-  s.tiles_y = (H + kPrioTile - 1) / kPrioTile;
+  s.pitch = (W + 3) & ~3;
+  s.t0x = (W + kT0 - 1) / kT0;
+  s.t0y = (H + kT0 - 1) / kT0;
+  s.t1x = (s.t0x + kT1 - 1) / kT1;
+  s.t1y = (s.t0y + kT1 - 1) / kT1;
   size_t n_omega = 0;
   for (int y = 0; y < H; ++y)
     for (int x = 0; x < W; ++x) n_omega += mask[(size_t)y * mask_stride + x] != 0;
@@ -250,12 +358,13 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
   const dim3 g = search_plain_grid(s);
   s.n_partial = (int)(g.x * g.y);
   const size_t n = (size_t)W * H;
-  if (!alloc_n(c, s.img, n) || !alloc_n(c, s.omega, n) || !alloc_n(c, s.gray, n) ||
+  if (!alloc_n(c, s.img, (size_t)s.pitch * H) || !alloc_n(c, s.omega, n) || !alloc_n(c, s.gray, n) ||
       !alloc_n(c, s.conf, n) || !alloc_n(c, s.count, n) || !alloc_n(c, s.prio, n) ||
-      !alloc_n(c, s.pconf, n) || !alloc_n(c, s.tiles, (size_t)s.tiles_x * s.tiles_y) ||
+      !alloc_n(c, s.pconf, n) || !alloc_n(c, s.tiles0, (size_t)s.t0x * s.t0y) ||
+      !alloc_n(c, s.tiles1, (size_t)s.t1x * s.t1y) ||
       !alloc_n(c, s.ctrl, 1) || !alloc_n(c, s.trace, (size_t)s.trace_cap) ||
       !alloc_n(c, s.partial, (size_t)(s.n_partial > 0 ? s.n_partial : 1)) ||
-      !alloc_n(c, c->sat, (size_t)(W + 1) * (H + 1)) || !alloc_n(c, c->rgb_stage, 3 * n) ||
+      !alloc_n(c, c->sat, (size_t)(W + 1) * (H + 1) + (size_t)sat_chunks(H) * W) || !alloc_n(c, c->rgb_stage, 3 * n) ||
       !alloc_n(c, c->mask_stage, n)) {
     g_last_error = "device allocation failed";
     return fail(INPAINT_ERR_NOMEM);
@@ -331,6 +440,7 @@ int inpaint_run(inpaint_ctx* c, int max_iters, int* iters_done, inpaint_step_inf
                 int trace_cap) {
   if (iters_done) *iters_done = 0;
   if (!c || (trace && trace_cap < 0)) return INPAINT_ERR_ARG;
+  if (c->h_err) *c->h_err = 0;
   int rc = read_ctrl(c);
   if (rc) return rc;
   if (c->h_ctrl->status != 0) return c->h_ctrl->status;
@@ -340,9 +450,23 @@ int inpaint_run(inpaint_ctx* c, int max_iters, int* iters_done, inpaint_step_inf
   // suffice: the device loop is bounded even if a kernel misbehaved.
   long long lim = (long long)start + c->h_ctrl->remaining;
   if (max_iters > 0 && (long long)start + max_iters < lim) lim = (long long)start + max_iters;
-  if ((rc = build_run_graph(c))) return rc;
   if ((rc = set_limit(c, lim > INT_MAX ? INT_MAX : (int)lim))) return rc;
-  CK(cudaGraphLaunch(c->run_exec, c->stream));
+  if (use_engine(c)) {
+    if (c->opt.debug_checks) {  // engine has no per-iteration hook: drive it one iteration at a time
+      for (long long i = start; i < lim; ++i) {
+        if ((rc = set_limit(c, (int)(i + 1)))) return rc;
+        if ((rc = run_engine(c))) return rc;
+        CK(launch_verify_count(c->st, c->stream));
+        if ((rc = read_ctrl(c))) return rc;
+        if (*c->h_err || c->h_ctrl->status != 0 || c->h_ctrl->remaining == 0) break;
+      }
+    } else if ((rc = run_engine(c))) {
+      return rc;
+    }
+  } else {
+    if ((rc = build_run_graph(c))) return rc;
+    CK(cudaGraphLaunch(c->run_exec, c->stream));
+  }
   if ((rc = set_limit(c, INT_MAX))) return rc;
   if ((rc = read_ctrl(c))) return rc;
   const int done = c->h_ctrl->iter - start;
@@ -355,6 +479,10 @@ int inpaint_run(inpaint_ctx* c, int max_iters, int* iters_done, inpaint_step_inf
                          cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
     }
+  }
+  if (c->h_err && *c->h_err) {
+    g_last_error = "a bounded device wait in the persistent engine gave up";
+    return INPAINT_ERR_TIMEOUT;
   }
   if (c->h_ctrl->status != 0) return c->h_ctrl->status;
   return INPAINT_OK;
@@ -409,6 +537,17 @@ int inpaint_info(const inpaint_ctx* c, int* width, int* height, int* patch_radiu
   if (patch_radius) *patch_radius = c->r;
   if (remaining) *remaining = c->h_ctrl->remaining;
   if (evals) *evals = c->h_ctrl->evals;
+  return INPAINT_OK;
+}
+
+int inpaint_loop_timing(const inpaint_ctx* c, uint64_t* search_ns, uint64_t* update_ns,
+                        int* iters) {
+  if (!c) return INPAINT_ERR_ARG;
+  int rc = read_ctrl(c);
+  if (rc) return rc;
+  if (search_ns) *search_ns = c->h_ctrl->t_search;
+  if (update_ns) *update_ns = c->h_ctrl->t_update;
+  if (iters) *iters = c->h_ctrl->timed_iters;
   return INPAINT_OK;
 }
 

@@ -1,8 +1,10 @@
 // Device-side state and helpers shared by the kernels of libinpaint.
 //
 // Data layout in HBM for one image of W x H pixels (patch radius r):
-//   img    uint32[W*H]   RGBA8 (R in the low byte, A = 0): one pixel per word,
-//                        so a pixel is one 32-bit load and byte-SIMD works on it
+//   img    uint32[H*pitch]  RGBA8 (R in the low byte, A = 0): one pixel per
+//                        word, so a pixel is one 32-bit load and byte-SIMD
+//                        works on it; pitch = W rounded up to 4 words so rows
+//                        start on 16-byte boundaries (TMA tiles need that)
 //   omega  uint8[W*H]    1 = pixel of the target region Omega (still unknown)
 //   gray   uint8[W*H]    integer luma of known pixels (0 under Omega)
 //   conf   double[W*H]   confidence C (Eq. 2), 0 under Omega
@@ -11,8 +13,9 @@
 //   prio   uint64[W*H]   priority key of a front pixel: bits(P(p)) + 1; 0 off
 //                        the front (P >= 0, so the bits order like the values)
 //   pconf  double[W*H]   C(p) of the last priority evaluation at p
-//   tiles  PrioBest[]    best (key, idx) per 32x32 tile of prio: the argmax
-//                        over the front touches only tiles, not pixels
+//   tiles0 PrioBest[]    best (key, idx) per 16x16-pixel tile of prio
+//   tiles1 PrioBest[]    best per 16x16 block of tiles0 (256x256 pixels): the
+//                        argmax over the front reads only these few entries
 //   ctrl   Ctrl          loop control block (selected p^, counters, status)
 //   trace  inpaint_step_info[trace_cap]   one record per iteration
 #pragma once
@@ -23,7 +26,8 @@
 
 namespace inp {
 
-constexpr int kPrioTile = 32;   // edge of a priority tile
+constexpr int kT0 = 16;         // edge of a level-0 priority tile (pixels)
+constexpr int kT1 = 16;         // edge of a level-1 tile (level-0 tiles)
 constexpr int kMaxRadius = 32;  // largest supported patch radius
 constexpr int kCountInvalid = 1 << 28;  // count of a centre whose patch leaves the image
 
@@ -59,12 +63,18 @@ struct Ctrl {
   double conf;     // C(p^) of the selected target
   unsigned long long evals;  // sum over iterations of n_cand * n_known
   inpaint_step_info last;    // record of the most recent iteration
+  // persistent-engine phase clocks (global timer, ns): search round (from the
+  // previous publish to the last arrival) and update phase, summed
+  unsigned long long t_search, t_update, t_last;
+  int timed_iters;
+  int pad1;
 };
 
 struct ImgState {
   int W, H, r;
+  int pitch;               // words per image row (W rounded up to 4)
   int cx0, cx1, cy0, cy1;  // candidate-centre rectangle (inclusive)
-  int tiles_x, tiles_y;
+  int t0x, t0y, t1x, t1y;  // level-0 / level-1 tile grid sizes
   int trace_cap;
   int n_partial;           // search CTAs writing partial[]
   uint32_t* img;
@@ -74,7 +84,8 @@ struct ImgState {
   int32_t* count;
   unsigned long long* prio;
   double* pconf;
-  PrioBest* tiles;
+  PrioBest* tiles0;
+  PrioBest* tiles1;
   Ctrl* ctrl;
   inpaint_step_info* trace;
   unsigned long long* partial;  // per-CTA best search key of the iteration
@@ -177,12 +188,113 @@ __device__ inline int block_sum_int(int v, int* scratch) {
   return scratch[0];
 }
 
+// ---- priority tiles: two-level argmax structure over the prio keys ----
+
+// Rescans level-0 tile (tx, ty) from the pixel keys; one warp.
+__device__ inline void warp_rescan_t0(const ImgState& s, int tx, int ty) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long k = 0ull;
+  int idx = 0x7fffffff;
+  for (int j = lane; j < kT0 * kT0; j += 32) {
+    const int x = tx * kT0 + (j & (kT0 - 1)), y = ty * kT0 + j / kT0;
+    if (x < s.W && y < s.H) {
+      const int i = y * s.W + x;
+      const unsigned long long kk = __ldcg(&s.prio[i]);
+      if (prio_better(kk, i, k, idx)) {
+        k = kk;
+        idx = i;
+      }
+    }
+  }
+  warp_best_prio(k, idx);
+  if (lane == 0) {
+    s.tiles0[ty * s.t0x + tx].key = k;
+    s.tiles0[ty * s.t0x + tx].idx = idx;
+  }
+}
+
+// Rescans level-1 tile (ux, uy) from the level-0 entries; one warp.
+__device__ inline void warp_rescan_t1(const ImgState& s, int ux, int uy) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long k = 0ull;
+  int idx = 0x7fffffff;
+  for (int j = lane; j < kT1 * kT1; j += 32) {
+    const int tx = ux * kT1 + (j & (kT1 - 1)), ty = uy * kT1 + j / kT1;
+    if (tx < s.t0x && ty < s.t0y) {
+      const unsigned long long bk = __ldcg(&s.tiles0[ty * s.t0x + tx].key);
+      const int bi = __ldcg(&s.tiles0[ty * s.t0x + tx].idx);
+      if (prio_better(bk, bi, k, idx)) {
+        k = bk;
+        idx = bi;
+      }
+    }
+  }
+  warp_best_prio(k, idx);
+  if (lane == 0) {
+    s.tiles1[uy * s.t1x + ux].key = k;
+    s.tiles1[uy * s.t1x + ux].idx = idx;
+  }
+}
+
+// Best front pixel of the whole image from the level-1 entries; one warp,
+// every lane gets the result.
+__device__ inline void warp_global_best(const ImgState& s, unsigned long long& k, int& idx) {
+  const int lane = threadIdx.x & 31;
+  k = 0ull;
+  idx = 0x7fffffff;
+  const int n = s.t1x * s.t1y;
+  for (int j = lane; j < n; j += 32) {
+    const unsigned long long bk = __ldcg(&s.tiles1[j].key);
+    const int bi = __ldcg(&s.tiles1[j].idx);
+    if (prio_better(bk, bi, k, idx)) {
+      k = bk;
+      idx = bi;
+    }
+  }
+  warp_best_prio(k, idx);
+}
+
+// After the prio keys of pixel rectangle [x0,x1] x [y0,y1] changed: refresh
+// the tiles over it.  Whole block; ends with a __syncthreads.
+__device__ inline void block_refresh_tiles(const ImgState& s, int x0, int x1, int y0, int y1) {
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int tx0 = x0 / kT0, tx1 = x1 / kT0, ty0 = y0 / kT0, ty1 = y1 / kT0;
+  const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
+  for (int t = w; t < nt; t += nw) warp_rescan_t0(s, tx0 + t % ntx, ty0 + t / ntx);
+  __syncthreads();
+  const int ux0 = tx0 / kT1, ux1 = tx1 / kT1, uy0 = ty0 / kT1, uy1 = ty1 / kT1;
+  const int nux = ux1 - ux0 + 1, nu = nux * (uy1 - uy0 + 1);
+  for (int t = w; t < nu; t += nw) warp_rescan_t1(s, ux0 + t % nux, uy0 + t / nux);
+  __syncthreads();
+}
+
+// Selection of the next target p^ (highest priority, lowest index on ties)
+// into the control block.  Called by warp 0 only.
+__device__ inline void warp_select(const ImgState& s) {
+  unsigned long long k;
+  int idx;
+  warp_global_best(s, k, idx);
+  if ((threadIdx.x & 31) == 0) {
+    Ctrl* c = s.ctrl;
+    if (k == 0ull) {
+      c->status = INPAINT_ERR_INTERNAL;  // Omega non-empty but no front
+    } else {
+      c->px = idx % s.W;
+      c->py = idx / s.W;
+      c->prio = __longlong_as_double((long long)(k - 1ull));
+      c->conf = __ldcg(&s.pconf[idx]);
+    }
+  }
+}
+
 // ---- host-side launchers (defined in the .cu files) ----
 cudaError_t launch_init(const ImgState& s, const uint8_t* rgb, int rgb_stride, const uint8_t* mask,
                         int mask_stride, int32_t* sat, int* omega_count, cudaStream_t st);
 cudaError_t launch_import(const ImgState& s, const uint8_t* rgb, const uint8_t* omega,
                           const double* conf, int32_t* sat, int* omega_count, cudaStream_t st);
+int sat_chunks(int H);  // the integral image needs (W+1)(H+1) + sat_chunks(H)*W ints
 cudaError_t prepare_search_plain(int r);
+cudaError_t launch_prio_init_fast(const ImgState& s, cudaStream_t st);  // r <= 8
 cudaError_t launch_search_plain(const ImgState& s, cudaStream_t st);
 dim3 search_plain_grid(const ImgState& s);
 cudaError_t launch_update(const ImgState& s, int do_fill, unsigned long long cond_handle,

@@ -105,29 +105,6 @@ __device__ inline void eval_pixel(const ImgState& s, int x, int y) {
   s.pconf[i] = c;
 }
 
-// Best (key, idx) of one 32x32 priority tile; the whole block calls it.
-__device__ void tile_best(const ImgState& s, int tx, int ty, PrioBest* scratch) {
-  unsigned long long k = 0ull;
-  int idx = 0x7fffffff;
-  const int x0 = tx * kPrioTile, y0 = ty * kPrioTile;
-  for (int j = threadIdx.x; j < kPrioTile * kPrioTile; j += blockDim.x) {
-    const int x = x0 + (j & (kPrioTile - 1)), y = y0 + j / kPrioTile;
-    if (x < s.W && y < s.H) {
-      const int i = y * s.W + x;
-      const unsigned long long kk = s.prio[i];
-      if (prio_better(kk, i, k, idx)) {
-        k = kk;
-        idx = i;
-      }
-    }
-  }
-  block_best_prio(k, idx, scratch);
-  if (threadIdx.x == 0) {
-    s.tiles[ty * s.tiles_x + tx].key = k;
-    s.tiles[ty * s.tiles_x + tx].idx = idx;
-  }
-}
-
 // ---------------------------------------------------------------- init
 
 __global__ void k_ctrl_init(Ctrl* c) {
@@ -142,6 +119,10 @@ __global__ void k_ctrl_init(Ctrl* c) {
   c->prio = 0.0;
   c->conf = 0.0;
   c->evals = 0ull;
+  c->t_search = 0ull;
+  c->t_update = 0ull;
+  c->t_last = 0ull;
+  c->timed_iters = 0;
 }
 
 // RGB (or RGBA words) + mask -> packed state; counts |Omega|.
@@ -156,7 +137,7 @@ __global__ void k_unpack(ImgState s, const uint8_t* rgb, int rgb_stride, const u
     const uint32_t w = pack_rgb(p[0], p[1], p[2]);
     const size_t i = (size_t)y * s.W + x;
     om = mask[(size_t)y * mask_stride + x] != 0;
-    s.img[i] = w;
+    s.img[(size_t)y * s.pitch + x] = w;
     s.omega[i] = (uint8_t)om;
     s.gray[i] = om ? 0 : (uint8_t)luma_word(w);
     s.conf[i] = om ? 0.0 : (conf_in ? conf_in[i] : 1.0);
@@ -166,39 +147,71 @@ __global__ void k_unpack(ImgState s, const uint8_t* rgb, int rgb_stride, const u
 }
 
 // Integral image of Omega: sat[y][x] = #Omega in [0,x) x [0,y), (W+1) x (H+1).
-__global__ void k_sat_cols(ImgState s, int32_t* sat) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int W1 = s.W + 1;
-  if (x < s.W) {
-    int run = 0;
-    sat[x + 1] = 0;
-    for (int y = 0; y < s.H; ++y) {
-      run += s.omega[(size_t)y * s.W + x];
-      sat[(size_t)(y + 1) * W1 + x + 1] = run;
-    }
-  }
-  if (x == 0)
-    for (int y = 0; y <= s.H; ++y) sat[(size_t)y * W1] = 0;
-}
+// Pass 1: prefix along each row (one warp per row).  Pass 2: prefix down each
+// column within chunks of kSatChunk rows.  Pass 3: exclusive prefix of the
+// chunk totals per column.  Pass 4: add each chunk's offset.
+constexpr int kSatChunk = 64;
 
 __global__ void k_sat_rows(ImgState s, int32_t* sat) {
   const int lane = threadIdx.x & 31;
-  const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1;
+  const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (y > s.H) return;
-  int32_t* row = sat + (size_t)y * (s.W + 1) + 1;
+  const int W1 = s.W + 1;
+  int32_t* row = sat + (size_t)y * W1;
+  if (y == 0) {
+    for (int x = lane; x < W1; x += 32) row[x] = 0;
+    return;
+  }
+  const uint8_t* om = s.omega + (size_t)(y - 1) * s.W;
+  if (lane == 0) row[0] = 0;
   int carry = 0;
   for (int base = 0; base < s.W; base += 32) {
     const int x = base + lane;
-    int v = x < s.W ? row[x] : 0;
+    int v = x < s.W ? (int)om[x] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, v, o);
       if (lane >= o) v += t;
     }
     v += carry;
-    if (x < s.W) row[x] = v;
+    if (x < s.W) row[x + 1] = v;
     carry = __shfl_sync(0xffffffffu, v, 31);
   }
+}
+
+__global__ void k_sat_cols_chunk(ImgState s, int32_t* sat, int32_t* tot) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ch = blockIdx.y;
+  if (x >= s.W) return;
+  const int W1 = s.W + 1;
+  const int y0 = 1 + ch * kSatChunk, y1 = min(s.H, ch * kSatChunk + kSatChunk);
+  int run = 0;
+  for (int y = y0; y <= y1; ++y) {
+    int32_t* p = sat + (size_t)y * W1 + x + 1;
+    run += *p;
+    *p = run;
+  }
+  tot[(size_t)ch * s.W + x] = run;
+}
+
+__global__ void k_sat_chunk_prefix(ImgState s, int32_t* tot, int nchunks) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= s.W) return;
+  int run = 0;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    int32_t* p = tot + (size_t)ch * s.W + x;
+    const int v = *p;
+    *p = run;
+    run += v;
+  }
+}
+
+__global__ void k_sat_cols_apply(ImgState s, int32_t* sat, const int32_t* tot) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y + 1 + kSatChunk;  // the first chunk needs no offset
+  if (x >= s.W || y > s.H) return;
+  const int ch = (y - 1) / kSatChunk;
+  sat[(size_t)y * (s.W + 1) + x + 1] += tot[(size_t)ch * s.W + x];
 }
 
 __device__ inline bool in_rect(const ImgState& s, int x, int y) {
@@ -232,9 +245,15 @@ __global__ void k_prio_all(ImgState s) {
   if (x < s.W) eval_pixel(s, x, y);
 }
 
-__global__ void k_tiles_all(ImgState s) {
-  __shared__ PrioBest scratch[32];
-  tile_best(s, blockIdx.x, blockIdx.y, scratch);
+// Level-0 tiles from the pixel keys, then level-1 tiles: one warp per tile.
+__global__ void k_tiles0_all(ImgState s) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t < s.t0x * s.t0y) warp_rescan_t0(s, t % s.t0x, t / s.t0x);
+}
+
+__global__ void k_tiles1_all(ImgState s) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t < s.t1x * s.t1y) warp_rescan_t1(s, t % s.t1x, t / s.t1x);
 }
 
 // ---------------------------------------------------------------- update
@@ -294,8 +313,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(ImgState s, int do_fill,
       if (tx >= 0 && tx < W && ty >= 0 && ty < H) {
         const size_t t = (size_t)ty * W + tx;
         if (s.omega[t]) {
-          const uint32_t w = s.img[(size_t)(qy + dy) * W + qx + dx];
-          s.img[t] = w;
+          const uint32_t w = s.img[(size_t)(qy + dy) * s.pitch + qx + dx];
+          s.img[(size_t)ty * s.pitch + tx] = w;
           s.gray[t] = (uint8_t)luma_word(w);
           s.conf[t] = cp;
           s.omega[t] = 0;
@@ -358,10 +377,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(ImgState s, int do_fill,
       if (x >= 0 && x < W && y >= 0 && y < H) eval_pixel(s, x, y);
     }
     __syncthreads();
-    const int tx0 = max(0, px - R2) / kPrioTile, tx1 = min(W - 1, px + R2) / kPrioTile;
-    const int ty0 = max(0, py - R2) / kPrioTile, ty1 = min(H - 1, py + R2) / kPrioTile;
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) tile_best(s, tx, ty, sm.pb);
+    block_refresh_tiles(s, max(0, px - R2), min(W - 1, px + R2), max(0, py - R2),
+                        min(H - 1, py + R2));
 
     remaining -= filled;
     if (filled == 0) {  // p^ must lie in Omega; stop rather than loop without progress
@@ -400,31 +417,9 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(ImgState s, int do_fill,
   }
 
   // Selection of the next target: highest priority on the front, lowest
-  // index on ties, from the per-tile maxima.
-  if (remaining > 0) {
-    unsigned long long k = 0ull;
-    int idx = 0x7fffffff;
-    const int ntiles = s.tiles_x * s.tiles_y;
-    for (int t = tid; t < ntiles; t += nt) {
-      const unsigned long long kk = s.tiles[t].key;
-      const int ii = s.tiles[t].idx;
-      if (prio_better(kk, ii, k, idx)) {
-        k = kk;
-        idx = ii;
-      }
-    }
-    block_best_prio(k, idx, sm.pb);
-    if (tid == 0) {
-      if (k == 0ull) {
-        c->status = INPAINT_ERR_INTERNAL;  // Omega non-empty but no front
-      } else {
-        c->px = idx % W;
-        c->py = idx / W;
-        c->prio = __longlong_as_double((long long)(k - 1ull));
-        c->conf = s.pconf[idx];
-      }
-    }
-  }
+  // index on ties, from the level-1 tile maxima.
+  if (remaining > 0 && tid < 32) warp_select(s);
+  __syncthreads();
   if (use_cond && tid == 0) cudaGraphSetConditional(cond, loop_active(c) ? 1u : 0u);
 }
 
@@ -457,7 +452,7 @@ __global__ void k_verify(ImgState s) {
 __global__ void k_export(ImgState s, uint8_t* rgb) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)s.W * s.H) return;
-  const uint32_t w = s.img[i];
+  const uint32_t w = s.img[(i / s.W) * s.pitch + i % s.W];
   rgb[3 * i] = (uint8_t)(w & 255u);
   rgb[3 * i + 1] = (uint8_t)((w >> 8) & 255u);
   rgb[3 * i + 2] = (uint8_t)((w >> 16) & 255u);
@@ -465,14 +460,26 @@ __global__ void k_export(ImgState s, uint8_t* rgb) {
 
 // ---------------------------------------------------------------- launchers
 
+int sat_chunks(int H) { return (H + kSatChunk - 1) / kSatChunk; }
+
 static cudaError_t init_tail(const ImgState& s, int32_t* sat, cudaStream_t st) {
   const int W = s.W, H = s.H;
-  k_sat_cols<<<(W + 255) / 256, 256, 0, st>>>(s, sat);
-  k_sat_rows<<<(H + 7) / 8, 256, 0, st>>>(s, sat);
+  int32_t* tot = sat + (size_t)(W + 1) * (H + 1);
+  const int nch = sat_chunks(H);
+  k_sat_rows<<<(H + 1 + 7) / 8, 256, 0, st>>>(s, sat);
+  k_sat_cols_chunk<<<dim3((W + 127) / 128, nch), 128, 0, st>>>(s, sat, tot);
+  k_sat_chunk_prefix<<<(W + 127) / 128, 128, 0, st>>>(s, tot, nch);
+  if (H > kSatChunk) k_sat_cols_apply<<<dim3((W + 127) / 128, H - kSatChunk), 128, 0, st>>>(s, sat, tot);
   const dim3 rows((W + 255) / 256, H);
   k_count<<<rows, 256, 0, st>>>(s, sat);
-  k_prio_all<<<rows, 256, 0, st>>>(s);
-  k_tiles_all<<<dim3(s.tiles_x, s.tiles_y), 256, 0, st>>>(s);
+  if (s.r <= 8) {
+    const cudaError_t e = launch_prio_init_fast(s, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    k_prio_all<<<rows, 256, 0, st>>>(s);
+  }
+  k_tiles0_all<<<(s.t0x * s.t0y + 7) / 8, 256, 0, st>>>(s);
+  k_tiles1_all<<<(s.t1x * s.t1y + 7) / 8, 256, 0, st>>>(s);
   k_update<<<1, kUpdThreads, 0, st>>>(s, 0, 0ull, 0);
   return cudaGetLastError();
 }

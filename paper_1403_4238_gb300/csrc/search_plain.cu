@@ -36,7 +36,7 @@ __device__ inline void stage_tile(const ImgState& s, uint32_t* dst, int x0, int 
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int yy = y0 + i / pitch, xx = x0 + i % pitch;
     uint32_t w = 0;
-    if (xx >= 0 && xx < s.W && yy >= 0 && yy < s.H) w = s.img[(size_t)yy * s.W + xx];
+    if (xx >= 0 && xx < s.W && yy >= 0 && yy < s.H) w = s.img[(size_t)yy * s.pitch + xx];
     dst[i] = w;
   }
 }
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kSearchThreads) k_search_plain(ImgState s) {
       if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H) {
         const size_t t = (size_t)ty * s.W + tx;
         if (!s.omega[t]) {
-          w = s.img[t];
+          w = s.img[(size_t)ty * s.pitch + tx];
           m |= 1u << dx;
         }
       }
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kGenThreads) k_search_generic(ImgState s) {
           const size_t t = (size_t)ty * s.W + tx;
           if (!s.omega[t]) {
             koff[n] = dy * SW + dx;
-            kval[n] = s.img[t];
+            kval[n] = s.img[(size_t)ty * s.pitch + tx];
             ++n;
           }
         }

@@ -48,13 +48,19 @@ def run_both(api, case, **kw):
     return ora, (rc, n, tr, out, m, info)
 
 
+LOOPS = ["engine", "graph"]
+
+
+@pytest.mark.parametrize("loop", LOOPS)
 @pytest.mark.parametrize("W,H,r,seed", [
     (20, 16, 1, 1), (24, 20, 2, 2), (33, 27, 3, 3), (40, 31, 4, 4), (47, 35, 5, 5),
     (52, 45, 6, 6), (61, 50, 7, 7), (70, 58, 8, 8), (75, 64, 9, 9), (90, 80, 12, 10),
 ])
-def test_tiny_full_runs_every_radius(api, W, H, r, seed):
+def test_tiny_full_runs_every_radius(api, W, H, r, seed, loop):
+    if loop == "engine" and r > 8:
+        loop = "auto"  # the engine covers r <= 8; larger radii use the graph loop
     case = synth.tiny(W, H, seed, r=r)
-    ora, (rc, n, tr, out, m, info) = run_both(api, case, debug=True)
+    ora, (rc, n, tr, out, m, info) = run_both(api, case, debug=True, loop=loop)
     assert ora.status == 0 and rc == 0
     assert n == ora.iters
     assert_trace_equal(tr, ora.trace)
@@ -62,9 +68,11 @@ def test_tiny_full_runs_every_radius(api, W, H, r, seed):
     assert m.sum() == 0 and info["evals"] == ora.evals
 
 
-def test_small_rect_config(api):
+@pytest.mark.parametrize("loop,tile_rows", [("engine", 1), ("engine", 2), ("engine", 4),
+                                             ("graph", 0)])
+def test_small_rect_config(api, loop, tile_rows):
     case = synth.small_rect()
-    ora, (rc, n, tr, out, m, info) = run_both(api, case, debug=True)
+    ora, (rc, n, tr, out, m, info) = run_both(api, case, debug=True, loop=loop, tile_rows=tile_rows)
     assert n == ora.iters == len(tr)
     assert_trace_equal(tr, ora.trace)
     assert np.array_equal(out, ora.rgb)
@@ -86,7 +94,8 @@ def test_step_by_step_equals_run(api):
         assert ip.step() is None  # DONE afterwards
 
 
-def test_border_masks_and_ragged_tiles(api):
+@pytest.mark.parametrize("loop", LOOPS)
+def test_border_masks_and_ragged_tiles(api, loop):
     # candidate grid not a multiple of the 128 x 8 tile; hole on two borders
     rng = np.random.default_rng(5)
     W, H, r = 203, 77, 4
@@ -96,14 +105,24 @@ def test_border_masks_and_ragged_tiles(api):
     mask[60:77, 0:6] = 1
     mask[30:40, 100:113] = rng.integers(0, 2, (10, 13)).astype(np.uint8)
     case = synth.Case("border", rgb, mask, r)
-    ora, (rc, n, tr, out, m, info) = run_both(api, case, debug=True)
+    ora, (rc, n, tr, out, m, info) = run_both(api, case, debug=True, loop=loop)
     assert_trace_equal(tr, ora.trace)
     assert np.array_equal(out, ora.rgb)
 
 
-def test_walkingman_like_config(api):
+@pytest.fixture(scope="module")
+def walkingman():
     case = synth.walkingman_like()
-    ora, (rc, n, tr, out, m, info) = run_both(api, case)
+    return case, oracle.run(case.rgb, case.mask, case.r)
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_walkingman_like_config(api, walkingman, loop):
+    case, ora = walkingman
+    with api.Inpainter(case.rgb, case.mask, case.r, loop=loop) as ip:
+        rc, n, tr = ip.run(trace=True)
+        out = ip.result()
+        info = ip.info()
     assert rc == 0 and n == ora.iters
     assert_trace_equal(tr, ora.trace)
     assert np.array_equal(out, ora.rgb)
@@ -116,7 +135,7 @@ def test_hd_blob_prefix_and_sampled_iterations(api):
     GPU states, and check the whole run's invariants."""
     case = synth.hd_blob()
     ora = oracle.run(case.rgb, case.mask, case.r, max_iters=2)
-    with api.Inpainter(case.rgb, case.mask, case.r) as ip:
+    with api.Inpainter(case.rgb, case.mask, case.r, loop="engine") as ip:
         rc, n, tr = ip.run(max_iters=2, trace=True)
         assert n == 2
         assert_trace_equal(tr, ora.trace)
@@ -164,11 +183,12 @@ def test_status_codes(api):
         assert ip.info()["remaining"] == 16 * 20 - 1
 
 
-def test_search_alpha_matches_oracle(api):
+@pytest.mark.parametrize("loop", LOOPS)
+def test_search_alpha_matches_oracle(api, loop):
     case = synth.small_rect(seed=21)
     for alpha in (0.6, 1.5):
         ora = oracle.run(case.rgb, case.mask, case.r, alpha=alpha)
-        with api.Inpainter(case.rgb, case.mask, case.r, alpha=alpha) as ip:
+        with api.Inpainter(case.rgb, case.mask, case.r, alpha=alpha, loop=loop) as ip:
             assert ip.search_rect() == oracle.search_rect(case.mask, case.r, alpha)
             rc, n, tr = ip.run(trace=True)
             if ora.status == 0:
