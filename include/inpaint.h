@@ -83,8 +83,9 @@ typedef struct {
                             the whole loop (patch_radius <= 8 only);
                             INPAINT_LOOP_GRAPH: a CUDA graph with a conditional while
                             node around [search kernel, update kernel] */
-  int tile_rows;         /* engine search unit height in candidate rows: 1, 2 or 4;
-                            0 = chosen by the library (autotuned table) */
+  int tile_rows;         /* engine search: candidate rows per warp in a search batch
+                            (a batch is 16 warps x rows x 128 candidate columns):
+                            1 or 2; 0 = chosen by the library */
 } inpaint_options;
 
 #define INPAINT_LOOP_AUTO 0

@@ -1,0 +1,7 @@
+// Persistent engine, fast update and priority-init kernels for patch radius 6
+// (one translation unit per radius so that the instantiations build in parallel).
+#include "engine_impl.cuh"
+
+namespace inp {
+const EngineFns* engine_fns_r6() { return engine_fns_for<6>(); }
+}  // namespace inp

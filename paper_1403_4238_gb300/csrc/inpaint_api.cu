@@ -7,8 +7,11 @@
 // [findBestPatch search -> copy/update + next selection] until the update
 // kernel reports an empty Omega, so no host round trip happens per iteration.
 #include <climits>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -176,14 +179,12 @@ bool use_engine(const inpaint_ctx* c) {
   return c->r <= 8;
 }
 
-// Search unit height: the tallest (best reuse of staged rows) that still
-// gives every warp of the grid about two units.
-int pick_tile_rows(const ImgState& s, int grid_warps) {
+// Candidate rows per warp in a search batch (a batch is 16 warps x rows x
+// 128 columns): 2 when every CTA still gets about two batches, else 1.
+int pick_rows_per_warp(const ImgState& s, int grid) {
   const int xb = s.r + ((s.cx0 - s.r) & ~3);
   const long long ncg = (s.cx1 - xb + 128) / 128, ch = s.cy1 - s.cy0 + 1;
-  for (int sr = 4; sr > 1; sr >>= 1)
-    if (ncg * ((ch + sr - 1) / sr) >= 2ll * grid_warps) return sr;
-  return 1;
+  return ncg * ((ch + 2 * kEngWarps - 1) / (2 * kEngWarps)) >= 2ll * grid ? 2 : 1;
 }
 
 int setup_engine(inpaint_ctx* c) {
@@ -192,18 +193,18 @@ int setup_engine(inpaint_ctx* c) {
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int sr = c->opt.tile_rows;
-  if (sr != 0 && sr != 1 && sr != 2 && sr != 4) {
-    g_last_error = "tile_rows must be 0, 1, 2 or 4";
+  if (sr != 0 && sr != 1 && sr != 2) {
+    g_last_error = "tile_rows must be 0, 1 or 2";
     return INPAINT_ERR_ARG;
   }
   int bps = 0;
-  CK(engine_occupancy(c->r, sr ? sr : 4, &bps));
+  CK(engine_occupancy(c->r, sr ? sr : 2, &bps));
   if (bps < 1) {
     g_last_error = "engine kernel does not fit on an SM";
     return INPAINT_ERR_UNSUPPORTED;
   }
   const int grid = sms * bps;
-  if (!sr) sr = pick_tile_rows(c->st, grid * kEngWarps);
+  if (!sr) sr = pick_rows_per_warp(c->st, grid);
   CK(engine_occupancy(c->r, sr, &bps));
   const int g2 = sms * (bps < 1 ? 1 : bps);
   c->eng_grid = g2 < grid ? g2 : grid;
@@ -365,11 +366,16 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
       !alloc_n(c, s.ctrl, 1) || !alloc_n(c, s.trace, (size_t)s.trace_cap) ||
       !alloc_n(c, s.partial, (size_t)(s.n_partial > 0 ? s.n_partial : 1)) ||
       !alloc_n(c, c->sat, (size_t)(W + 1) * (H + 1) + (size_t)sat_chunks(H) * W) || !alloc_n(c, c->rgb_stage, 3 * n) ||
-      !alloc_n(c, c->mask_stage, n)) {
+      !alloc_n(c, c->mask_stage, n) || !alloc_n(c, s.spec, 1)) {
     g_last_error = "device allocation failed";
     return fail(INPAINT_ERR_NOMEM);
   }
   if (prepare_search_plain(r) != cudaSuccess) return fail(INPAINT_ERR_CUDA);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || !(s.dtab = data_term_table(dev)))
+      return fail(INPAINT_ERR_CUDA);
+  }
   *out = c;
   rc = inpaint_reset(c, rgb, rgb_stride, mask, mask_stride, 0);
   if (rc < 0) {
@@ -380,6 +386,32 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
 }
 
 }  // namespace
+
+// Per-device table of the data term D = (dot / sqrt(nn)) / 510 (Eq. 2 with
+// alpha = 255 and the factor 2 of the central difference), evaluated with
+// the same IEEE double operations the kernels would use (sqrt and division
+// are correctly rounded on host and device alike).  Built once per device
+// and kept for the life of the process.
+const double* inp::data_term_table(int device) {
+  static std::mutex mu;
+  static std::map<int, double*> tabs;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = tabs.find(device);
+  if (it != tabs.end()) return it->second;
+  std::vector<double> h((size_t)kDTabRows * kDTabCols);
+  for (int r = 0; r < kDTabRows; ++r) {
+    const double root = std::sqrt((double)kDTabNN[r]);
+    for (int dot = 0; dot < kDTabCols; ++dot) h[(size_t)r * kDTabCols + dot] = ((double)dot / root) / 510.0;
+  }
+  double* d = nullptr;
+  if (cudaMalloc(&d, h.size() * sizeof(double)) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  tabs[device] = d;
+  return d;
+}
 
 extern "C" {
 

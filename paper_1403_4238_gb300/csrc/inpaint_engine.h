@@ -7,7 +7,7 @@
 
 namespace inp {
 
-constexpr int kEngThreads = 256;
+constexpr int kEngThreads = 512;
 constexpr int kEngWarps = kEngThreads / 32;
 
 // Per-team synchronisation words (global memory).
@@ -30,10 +30,26 @@ struct EngineArgs {
   unsigned long long wait_limit_ns;
 };
 
+// Kernels of one patch radius (engine_r<R>.cu).
+struct EngineFns {
+  cudaError_t (*launch)(int srw, const EngineArgs& ea, int grid, cudaStream_t st);
+  cudaError_t (*occupancy)(int srw, int* blocks_per_sm);
+  cudaError_t (*update_fast)(const ImgState& s, unsigned long long cond, int use_cond,
+                             cudaStream_t st);
+  cudaError_t (*prio_init)(const ImgState& s, cudaStream_t st);
+};
+const EngineFns* engine_fns_r1();
+const EngineFns* engine_fns_r2();
+const EngineFns* engine_fns_r3();
+const EngineFns* engine_fns_r4();
+const EngineFns* engine_fns_r5();
+const EngineFns* engine_fns_r6();
+const EngineFns* engine_fns_r7();
+const EngineFns* engine_fns_r8();
+
 cudaError_t engine_occupancy(int r, int sr, int* blocks_per_sm);
 cudaError_t engine_launch(int r, int sr, const EngineArgs& ea, int grid, cudaStream_t st);
-size_t engine_smem_bytes(int r, int sr);
-int make_image_tmap(const ImgState& s, int sr, CUtensorMap* out);
+int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out);
 cudaError_t launch_update_fast(const ImgState& s, unsigned long long cond, int use_cond,
                                cudaStream_t st);
 

@@ -70,6 +70,43 @@ struct Ctrl {
   int pad1;
 };
 
+// Output of the speculative phase of an iteration (see update_fast.cuh): for
+// each pixel of the (4R+3)^2 window around p^, the post-fill confidence term
+// and front normal.  Sized for R <= 8.
+constexpr int kSpecMax = 35 * 35;
+constexpr int kSpecOutside = -2;   // window pixel outside the image
+constexpr int kSpecNotFront = -1;  // in the image, not on the post-fill front
+struct SpecBuf {
+  double C[kSpecMax];
+  int nrm[kSpecMax];
+  int iter;    // iteration described
+  int filled;  // pixels that iteration fills
+};
+
+// Data-term table: D = (dot / sqrt(nn)) / 510 for every |n|^2 = nn a Sobel
+// normal of a binary mask can take (nx, ny in [-4, 4]) and dot in [0, 2040].
+constexpr int kDTabRows = 14;
+constexpr int kDTabCols = 2041;
+__host__ __device__ inline int dtab_code(int nn) {
+  switch (nn) {
+    case 1: return 0;
+    case 2: return 1;
+    case 4: return 2;
+    case 5: return 3;
+    case 8: return 4;
+    case 9: return 5;
+    case 10: return 6;
+    case 13: return 7;
+    case 16: return 8;
+    case 17: return 9;
+    case 18: return 10;
+    case 20: return 11;
+    case 25: return 12;
+    default: return 13;  // 32, the largest
+  }
+}
+constexpr int kDTabNN[kDTabRows] = {1, 2, 4, 5, 8, 9, 10, 13, 16, 17, 18, 20, 25, 32};
+
 struct ImgState {
   int W, H, r;
   int pitch;               // words per image row (W rounded up to 4)
@@ -89,6 +126,8 @@ struct ImgState {
   Ctrl* ctrl;
   inpaint_step_info* trace;
   unsigned long long* partial;  // per-CTA best search key of the iteration
+  SpecBuf* spec;                // speculative-phase output (R <= 8)
+  const double* dtab;           // data-term table (device, shared by contexts)
 };
 
 __host__ __device__ inline uint32_t pack_rgb(uint32_t r, uint32_t g, uint32_t b) {
@@ -295,6 +334,7 @@ cudaError_t launch_import(const ImgState& s, const uint8_t* rgb, const uint8_t* 
 int sat_chunks(int H);  // the integral image needs (W+1)(H+1) + sat_chunks(H)*W ints
 cudaError_t prepare_search_plain(int r);
 cudaError_t launch_prio_init_fast(const ImgState& s, cudaStream_t st);  // r <= 8
+const double* data_term_table(int device);  // per-device table, built on first use
 cudaError_t launch_search_plain(const ImgState& s, cudaStream_t st);
 dim3 search_plain_grid(const ImgState& s);
 cudaError_t launch_update(const ImgState& s, int do_fill, unsigned long long cond_handle,

@@ -1,15 +1,25 @@
-// Copy/update phase of one fill iteration for patch radius R <= 8, executed
-// by a single CTA (the update kernel of the graph loop, or the last CTA of a
-// search round inside the persistent engine).
+// Copy/update phase of one fill iteration for patch radius R <= 8.
 //
 // Sec. 3: after findBestPatch the pixels of Psi_q~ are copied into the
 // unknown part of Psi_p^, those pixels take the confidence C(p^), and the
 // priorities P(p) = C(p) D(p) (Eq. 1-2) that depend on them are recomputed
-// before the next target is selected.  Everything this touches lies within
-// 3R+2 pixels of p^, so that neighbourhood (mask, grey level, confidence) is
-// staged in shared memory once; the priorities of the front pixels within
-// 2R+1 of p^ are then evaluated from shared memory, each in one thread with
-// the confidence sum in row-major patch order (bit-identical to the CPU).
+// before the next target is selected.  Everything involved lies within 3R+2
+// pixels of p^, so that neighbourhood is staged in shared memory.
+//
+// The work is split in two phases.  Which pixels are filled (Psi_p^ ∩ Omega)
+// and the confidence they receive (C(p^)) are known as soon as p^ is
+// selected; only their colours depend on the search result q~.  So the
+// *speculative phase* (spec_phase) runs while the search is still going: it
+// builds the post-fill mask and confidences, finds the post-fill front pixels
+// within 2R+1 of p^, and evaluates their confidence terms C(p) -- the
+// sequential FP64 sums, in row-major patch order (the part with the longest
+// dependency chain) -- and their front normals.  The *update phase*
+// (update_phase) then only copies the pixels, recomputes the isophotes from
+// the new grey levels, and combines them into the data terms D(p) and the
+// priorities.  The data term D = (|dot| / sqrt(nn)) / 510 takes one of a
+// finite set of values (nn = |n|^2 <= 32, |dot| <= 2040); the library
+// evaluates that set once with the same IEEE operations and reads it back
+// here, which gives the same bits as evaluating the expression.
 #pragma once
 #include "inpaint_internal.cuh"
 
@@ -29,45 +39,24 @@ template <int R>
 struct __align__(16) UpdSmem {
   using G = UpdGeom<R>;
   double cf[G::NS * G::NS];
-  int mag[G::NS * G::NS];  // isophote |grad|^2 at a local pixel, -1 if not eligible
-  int gxy[G::NS * G::NS];  // (gx + 512) << 16 | (gy + 512)
+  double sC[G::NW * G::NW];  // post-fill C(p) of the window (from the speculative phase)
+  int snrm[G::NW * G::NW];   // packed normal, or kSpecNotFront / kSpecOutside
+  int mag[G::NS * G::NS];    // isophote |grad|^2 at a local pixel, -1 if not eligible
+  int gxy[G::NS * G::NS];    // (gx + 512) << 16 | (gy + 512)
   int fsat[(G::P + 1) * (G::P + 1)];
-  uint16_t flist[G::NW * G::NW];
   uint8_t om[G::NS * G::NS];  // 0 known, 1 Omega, 2 outside the image
   uint8_t gr[G::NS * G::NS];
   uint8_t filled[G::P * G::P];
-  int nfront;
   unsigned long long red64[32];
-  PrioBest redpb[32];
   int red32[32];
 };
 
-__device__ inline int ldcg_i(const int* p) { return __ldcg(p); }
-
-// P(p) of Eq. 1-2 from the staged neighbourhood; (lx, ly) are p's local
-// coordinates, (x, y) its image coordinates.
+// Sobel normal of the Omega indicator at local (lx, ly) = image (x, y),
+// replicated image borders, packed as (nx + 8) << 8 | (ny + 8).
 template <int R>
-__device__ inline double prio_local(const UpdSmem<R>& sm, const ImgState& s, int lx, int ly, int x,
-                                    int y, double* c_out) {
-  using G = UpdGeom<R>;
-  constexpr int NS = G::NS;
-  double sum = 0.0;
-  int n_in = 0;
-#pragma unroll 1
-  for (int dy = -R; dy <= R; ++dy) {
-#pragma unroll
-    for (int dx = -R; dx <= R; ++dx) {
-      const int l = (ly + dy) * NS + lx + dx;
-      const int o = sm.om[l];
-      if (o != 2) {
-        ++n_in;
-        if (o == 0) sum = __dadd_rn(sum, sm.cf[l]);
-      }
-    }
-  }
-  const double c = __ddiv_rn(sum, (double)n_in);
-
-  // Sobel of the Omega indicator with replicated image borders.
+__device__ inline int normal_local(const UpdSmem<R>& sm, const ImgState& s, int lx, int ly, int x,
+                                   int y) {
+  constexpr int NS = UpdGeom<R>::NS;
   const int xl = x > 0 ? -1 : 0, xr = x < s.W - 1 ? 1 : 0;
   const int yu = y > 0 ? -1 : 0, yd = y < s.H - 1 ? 1 : 0;
   auto M = [&](int ox, int oy) { return sm.om[(ly + oy) * NS + lx + ox] == 1 ? 1 : 0; };
@@ -76,8 +65,31 @@ __device__ inline double prio_local(const UpdSmem<R>& sm, const ImgState& s, int
   const int m_ld = M(xl, yd), m_cd = M(0, yd), m_rd = M(xr, yd);
   const int nx = (m_ru + 2 * m_rc + m_rd) - (m_lu + 2 * m_lc + m_ld);
   const int ny = (m_ld + 2 * m_cd + m_rd) - (m_lu + 2 * m_cu + m_ru);
+  return ((nx + 8) << 8) | (ny + 8);
+}
 
-  // Isophote: strongest precomputed gradient in Psi_p, first in row-major order.
+// C(p) of Eq. 2: the known part of Psi_p summed in row-major order, over the
+// in-image area.  Unknown and out-of-image entries hold +0.0 in sm.cf, and
+// adding +0.0 to a non-negative double leaves it unchanged, so summing every
+// entry gives exactly the sum over the known pixels.
+template <int R>
+__device__ inline double conf_local(const UpdSmem<R>& sm, const ImgState& s, int lx, int ly, int x,
+                                    int y) {
+  constexpr int NS = UpdGeom<R>::NS;
+  double sum = 0.0;
+#pragma unroll 1
+  for (int dy = -R; dy <= R; ++dy) {
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) sum = __dadd_rn(sum, sm.cf[(ly + dy) * NS + lx + dx]);
+  }
+  const int n_in = (min(x + R, s.W - 1) - max(x - R, 0) + 1) * (min(y + R, s.H - 1) - max(y - R, 0) + 1);
+  return __ddiv_rn(sum, (double)n_in);
+}
+
+// Strongest precomputed isophote in Psi_p, first in row-major order.
+template <int R>
+__device__ inline void isophote_local(const UpdSmem<R>& sm, int lx, int ly, int* gx, int* gy) {
+  constexpr int NS = UpdGeom<R>::NS;
   int best = -1, bl = 0;
 #pragma unroll 1
   for (int dy = -R; dy <= R; ++dy) {
@@ -91,24 +103,41 @@ __device__ inline double prio_local(const UpdSmem<R>& sm, const ImgState& s, int
       }
     }
   }
-  int gx = 0, gy = 0;
+  *gx = 0;
+  *gy = 0;
   if (best >= 0) {
     const int g = sm.gxy[bl];
-    gx = (g >> 16) - 512;
-    gy = (g & 0xffff) - 512;
+    *gx = (g >> 16) - 512;
+    *gy = (g & 0xffff) - 512;
   }
-  int dot = (-gy) * nx + gx * ny;
-  dot = dot < 0 ? -dot : dot;
-  const int nn = nx * nx + ny * ny;
-  double d = 0.0;
-  if (nn != 0) d = __ddiv_rn(__ddiv_rn((double)dot, __dsqrt_rn((double)nn)), 510.0);
-  *c_out = c;
-  return __dmul_rn(c, d);
 }
 
+__device__ inline int dot_abs(int gx, int gy, int nrm) {
+  const int nx = (nrm >> 8) - 8, ny = (nrm & 0xff) - 8;
+  const int d = (-gy) * nx + gx * ny;
+  return d < 0 ? -d : d;
+}
 
-// Stages mask / grey / confidence of the NS x NS neighbourhood of (cx, cy).
-template <int R>
+__device__ inline int nn_of(int nrm) {
+  const int nx = (nrm >> 8) - 8, ny = (nrm & 0xff) - 8;
+  return nx * nx + ny * ny;
+}
+
+// D of Eq. 2 evaluated directly (initialisation).
+__device__ inline double data_term_direct(int dot, int nn) {
+  if (nn == 0) return 0.0;
+  return __ddiv_rn(__ddiv_rn((double)dot, __dsqrt_rn((double)nn)), 510.0);
+}
+
+// D from the precomputed table (same bits as data_term_direct).
+__device__ inline double data_term_table(const ImgState& s, int dot, int nn) {
+  if (nn == 0) return 0.0;
+  return __ldg(&s.dtab[dtab_code(nn) * kDTabCols + dot]);
+}
+
+// Stages the NS x NS neighbourhood of (cx, cy): mask (2 outside the image),
+// optionally grey levels and confidences (+0.0 under Omega and outside).
+template <int R, bool GRAY, bool CONF>
 __device__ inline void stage_nbhd(const ImgState& s, int cx, int cy, UpdSmem<R>& sm) {
   using G = UpdGeom<R>;
   constexpr int RB = G::RB, NS = G::NS;
@@ -119,12 +148,12 @@ __device__ inline void stage_nbhd(const ImgState& s, int cx, int cy, UpdSmem<R>&
     if (x >= 0 && x < s.W && y >= 0 && y < s.H) {
       const size_t q = (size_t)y * s.W + x;
       o = __ldcg(&s.omega[q]);
-      g = __ldcg(&s.gray[q]);
-      cf = __ldcg(&s.conf[q]);
+      if (GRAY) g = __ldcg(&s.gray[q]);
+      if (CONF) cf = o ? 0.0 : __ldcg(&s.conf[q]);
     }
     sm.om[i] = o;
-    sm.gr[i] = g;
-    sm.cf[i] = cf;
+    if (GRAY) sm.gr[i] = g;
+    if (CONF) sm.cf[i] = cf;
   }
 }
 
@@ -148,60 +177,91 @@ __device__ inline void stage_isophotes(UpdSmem<R>& sm) {
   }
 }
 
-// Front pixels of the NW x NW window around (cx, cy) go to sm.flist; the
-// other in-image window pixels get priority key 0.  sm.nfront must be 0.
+__device__ inline bool front_local(const uint8_t* om, int l, int NS) {
+  return om[l] == 1 && (om[l - 1] == 0 || om[l + 1] == 0 || om[l - NS] == 0 || om[l + NS] == 0);
+}
+
+// Initial priorities, one CTA per NW x NW window of the image (direct
+// evaluation of every term).
 template <int R>
-__device__ inline void window_front(const ImgState& s, int cx, int cy, UpdSmem<R>& sm) {
+__global__ void __launch_bounds__(256, 2) k_prio_init_fast(ImgState s) {
   using G = UpdGeom<R>;
   constexpr int RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW;
+  extern __shared__ __align__(16) uint8_t sm_raw[];
+  UpdSmem<R>& sm = *reinterpret_cast<UpdSmem<R>*>(sm_raw);
+  const int cx = R2 + blockIdx.x * NW, cy = R2 + blockIdx.y * NW;
+  stage_nbhd<R, true, true>(s, cx, cy, sm);
+  __syncthreads();
+  stage_isophotes<R>(sm);
+  __syncthreads();
   for (int i = threadIdx.x; i < NW * NW; i += blockDim.x) {
     const int wx = i % NW - R2, wy = i / NW - R2;
-    const int l = (RB + wy) * NS + RB + wx;
+    const int lx = RB + wx, ly = RB + wy, l = ly * NS + lx;
     if (sm.om[l] == 2) continue;
-    const bool front = sm.om[l] == 1 && (sm.om[l - 1] == 0 || sm.om[l + 1] == 0 ||
-                                         sm.om[l - NS] == 0 || sm.om[l + NS] == 0);
-    if (front) {
-      sm.flist[atomicAdd(&sm.nfront, 1)] = (uint16_t)i;
-    } else {
-      const size_t p = (size_t)(cy + wy) * s.W + cx + wx;
-      s.prio[p] = 0ull;
-      s.pconf[p] = 0.0;
+    const int x = cx + wx, y = cy + wy;
+    unsigned long long key = 0ull;
+    double c = 0.0;
+    if (front_local(sm.om, l, NS)) {
+      c = conf_local<R>(sm, s, lx, ly, x, y);
+      const int nrm = normal_local<R>(sm, s, lx, ly, x, y);
+      int gx, gy;
+      isophote_local<R>(sm, lx, ly, &gx, &gy);
+      const double d = data_term_direct(dot_abs(gx, gy, nrm), nn_of(nrm));
+      key = (unsigned long long)__double_as_longlong(__dmul_rn(c, d)) + 1ull;
     }
+    const size_t p = (size_t)y * s.W + x;
+    s.prio[p] = key;
+    s.pconf[p] = c;
   }
 }
 
-// Priority key of front-list entry i of the window around (cx, cy).
+// Speculative phase: post-fill front, normals and confidence terms of the
+// window around p^, written to s.spec.  Whole block.
 template <int R>
-__device__ inline void window_prio(const ImgState& s, int cx, int cy, const UpdSmem<R>& sm, int i) {
+__device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm) {
   using G = UpdGeom<R>;
-  constexpr int RB = G::RB, R2 = G::R2, NW = G::NW;
-  const int wi = sm.flist[i];
-  const int wx = wi % NW - R2, wy = wi / NW - R2;
-  double cc;
-  const double pr = prio_local<R>(sm, s, RB + wx, RB + wy, cx + wx, cy + wy, &cc);
-  const size_t p = (size_t)(cy + wy) * s.W + cx + wx;
-  s.prio[p] = (unsigned long long)__double_as_longlong(pr) + 1ull;
-  s.pconf[p] = cc;
+  constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW;
+  const Ctrl* c = s.ctrl;
+  const int px = __ldcg(&c->px), py = __ldcg(&c->py), it = __ldcg(&c->iter);
+  const double cp = __ldcg(&c->conf);
+  stage_nbhd<R, false, true>(s, px, py, sm);
+  __syncthreads();
+  int my = 0;
+  for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+    const int l = (RB + i / P - R) * NS + RB + i % P - R;
+    if (sm.om[l] == 1) {
+      sm.om[l] = 0;
+      sm.cf[l] = cp;
+      ++my;
+    }
+  }
+  const int filled = block_sum_int(my, sm.red32);  // includes __syncthreads
+  SpecBuf* sp = s.spec;
+  for (int i = threadIdx.x; i < NW * NW; i += blockDim.x) {
+    const int wx = i % NW - R2, wy = i / NW - R2;
+    const int lx = RB + wx, ly = RB + wy, l = ly * NS + lx;
+    int nrm = kSpecOutside;
+    double cc = 0.0;
+    if (sm.om[l] != 2) {
+      nrm = kSpecNotFront;
+      if (front_local(sm.om, l, NS)) {
+        const int x = px + wx, y = py + wy;
+        cc = conf_local<R>(sm, s, lx, ly, x, y);
+        nrm = normal_local<R>(sm, s, lx, ly, x, y);
+      }
+    }
+    sp->C[i] = cc;
+    sp->nrm[i] = nrm;
+  }
+  if (threadIdx.x == 0) {
+    sp->iter = it;
+    sp->filled = filled;
+  }
 }
 
-// Initial priorities, one CTA per NW x NW window of the image.
-template <int R>
-__global__ void __launch_bounds__(256) k_prio_init_fast(ImgState s) {
-  using G = UpdGeom<R>;
-  extern __shared__ __align__(16) uint8_t sm_raw[];
-  UpdSmem<R>& sm = *reinterpret_cast<UpdSmem<R>*>(sm_raw);
-  const int cx = G::R2 + blockIdx.x * G::NW, cy = G::R2 + blockIdx.y * G::NW;
-  if (threadIdx.x == 0) sm.nfront = 0;
-  stage_nbhd<R>(s, cx, cy, sm);
-  __syncthreads();
-  stage_isophotes<R>(sm);
-  window_front<R>(s, cx, cy, sm);
-  __syncthreads();
-  for (int i = threadIdx.x; i < sm.nfront; i += blockDim.x) window_prio<R>(s, cx, cy, sm, i);
-}
-
-// Returns false (status already written) when no source patch exists or the
-// state is inconsistent; true when the iteration was applied.  Whole block.
+// Update phase: applies the iteration whose best source key is the minimum
+// of partial[0..n_partial).  Returns false (status written) when there is no
+// source patch or the state is inconsistent.  Whole block.
 template <int R>
 __device__ bool update_phase(const ImgState& s, const unsigned long long* partial, int n_partial,
                              UpdSmem<R>& sm) {
@@ -214,15 +274,20 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const double cp = __ldcg(&c->conf), pp = __ldcg(&c->prio);
   const int n_cand = __ldcg(&c->n_valid), it = __ldcg(&c->iter);
   int remaining = __ldcg(&c->remaining);
+  const SpecBuf* sp = s.spec;
 
-  // U0 + U1: best source key over the search CTAs; stage the neighbourhood.
+  // best source key, staged mask + grey, speculative window terms
   unsigned long long best = ~0ull;
   for (int i = tid; i < n_partial; i += nt) {
     const unsigned long long v = __ldcg(&partial[i]);
     best = v < best ? v : best;
   }
-  stage_nbhd<R>(s, px, py, sm);
-  if (tid == 0) sm.nfront = 0;
+  stage_nbhd<R, true, false>(s, px, py, sm);
+  for (int i = tid; i < NW * NW; i += nt) {
+    sm.sC[i] = __ldcg(&sp->C[i]);
+    sm.snrm[i] = __ldcg(&sp->nrm[i]);
+  }
+  const int spec_iter = __ldcg(&sp->iter), spec_filled = __ldcg(&sp->filled);
   best = block_min_u64(best, sm.red64);
   if (best == ~0ull) {
     if (tid == 0) c->status = INPAINT_ERR_NO_SOURCE;
@@ -232,7 +297,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const int q = (int)(best & 0xffffffffull);
   const int qx = q % W, qy = q / W;
 
-  // U2: copy the unknown in-image part of Psi_p^ from Psi_q~.
+  // copy the unknown in-image part of Psi_p^ from Psi_q~
   int my_filled = 0;
   for (int i = tid; i < P * P; i += nt) {
     const int dy = i / P - R, dx = i % P - R;
@@ -249,22 +314,21 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       s.omega[t] = 0;
       sm.om[l] = 0;
       sm.gr[l] = g;
-      sm.cf[l] = cp;
       f = 1;
       ++my_filled;
     }
     sm.filled[i] = f;
   }
   const int filled = block_sum_int(my_filled, sm.red32);
-  if (filled == 0) {  // p^ must lie in Omega
-    if (tid == 0) c->status = INPAINT_ERR_INTERNAL;
+  if (filled == 0 || spec_iter != it || spec_filled != filled) {
+    if (tid == 0) c->status = INPAINT_ERR_INTERNAL;  // p^ not in Omega, or stale speculation
     return false;
   }
   const int nx_in = min(px + R, W - 1) - max(px - R, 0) + 1;
   const int ny_in = min(py + R, H - 1) - max(py - R, 0) + 1;
   const int n_known = nx_in * ny_in - filled;
 
-  // U3: isophote candidates, integral image of the filled flags, front list.
+  // isophotes of the new grey levels; integral image of the filled flags
   stage_isophotes<R>(sm);
   if (tid < 32) {
     constexpr int P1 = P + 1;
@@ -284,17 +348,29 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     for (int u = tid + 1; u <= P; u += 32)
       for (int v = 2; v <= P; ++v) sm.fsat[v * P1 + u] += sm.fsat[(v - 1) * P1 + u];
   }
-  window_front<R>(s, px, py, sm);
   __syncthreads();
 
-  // U4: validity counts around p^ and the priorities of the front pixels.
+  // priorities of the window and validity counts around p^
   int newly = 0;
-  const int nfront = sm.nfront;
-  for (int i = tid; i < NC * NC + nfront; i += nt) {
-    if (i < nfront) {
-      window_prio<R>(s, px, py, sm, i);
+  for (int i = tid; i < NW * NW + NC * NC; i += nt) {
+    if (i < NW * NW) {
+      const int nrm = sm.snrm[i];
+      if (nrm == kSpecOutside) continue;
+      const int wx = i % NW - R2, wy = i / NW - R2;
+      const size_t p = (size_t)(py + wy) * W + px + wx;
+      unsigned long long key = 0ull;
+      double cc = 0.0;
+      if (nrm != kSpecNotFront) {
+        int gx, gy;
+        isophote_local<R>(sm, RB + wx, RB + wy, &gx, &gy);
+        cc = sm.sC[i];
+        const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
+        key = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
+      }
+      s.prio[p] = key;
+      s.pconf[p] = cc;
     } else {
-      const int j = i - nfront;
+      const int j = i - NW * NW;
       const int wy = j / NC - 2 * R, wx = j % NC - 2 * R;
       const int x = px + wx, y = py + wy;
       if (x < 0 || x >= W || y < 0 || y >= H) continue;
@@ -313,7 +389,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   }
   newly = block_sum_int(newly, sm.red32);
 
-  // U5: tiles over the window, then the next target.
+  // tiles over the window, then the next target
   block_refresh_tiles(s, max(0, px - R2), min(W - 1, px + R2), max(0, py - R2), min(H - 1, py + R2));
   remaining -= filled;
   if (tid == 0) {

@@ -68,8 +68,7 @@ def test_tiny_full_runs_every_radius(api, W, H, r, seed, loop):
     assert m.sum() == 0 and info["evals"] == ora.evals
 
 
-@pytest.mark.parametrize("loop,tile_rows", [("engine", 1), ("engine", 2), ("engine", 4),
-                                             ("graph", 0)])
+@pytest.mark.parametrize("loop,tile_rows", [("engine", 1), ("engine", 2), ("graph", 0)])
 def test_small_rect_config(api, loop, tile_rows):
     case = synth.small_rect()
     ora, (rc, n, tr, out, m, info) = run_both(api, case, debug=True, loop=loop, tile_rows=tile_rows)
