@@ -182,6 +182,37 @@ int inpaint_loop_timing(const inpaint_ctx* ctx, uint64_t* search_ns, uint64_t* u
 /* Candidate-centre rectangle [x0,x1] x [y0,y1] the context searches. */
 int inpaint_search_rect(const inpaint_ctx* ctx, int* x0, int* x1, int* y0, int* y1);
 
+/* findBestPatch for a single target patch, allocating no device memory.
+ * The paper has no counterpart: this is for callers that cannot call
+ * cudaMalloc -- a serving process whose device memory is reserved up front
+ * by another framework's allocator, work issued while a stream is being
+ * captured into a graph with a fixed memory plan, or a real-time loop that
+ * forbids allocation after start-up.  The caller passes its own device
+ * buffers; the only scratch the search needs (one partial result per CTA and
+ * a ticket counter) is a fixed array inside the library, which every GPU
+ * that loads the library holds until the process exits.
+ *   d_rgb:  device, dense W x H x 3 bytes (RGB); d_mask: device, dense W x H
+ *           bytes, nonzero = unknown (Omega).
+ *   patch_radius 1..8; (px, py): target centre, inside the image.
+ *   d_best_key: device uint64, receives (SSD << 32) | (qy * W + qx) of the
+ *           fully-known in-image candidate patch with the lowest SSD over the
+ *           known in-image pixels of the target patch (lowest index on ties),
+ *           or UINT64_MAX if there is none.
+ *   cuda_stream: cudaStream_t of the work (NULL = legacy default stream).
+ * Limit: the interior (W - 2r) x (H - 2r) must fit in 4096 tiles of 8 rows x
+ * 128 columns of candidates (e.g. 4096 x 1024 or 2048 x 2048 pixels); larger
+ * images are rejected with INPAINT_ERR_ARG and a message in
+ * inpaint_last_error().  The first call on a device looks up the scratch's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call on a device shares the same scratch, which
+ * keeps the last call's contents (the ticket is cleared at the start of each
+ * call): calls that overlap on the GPU race and must be serialised by the
+ * caller (one stream, or events).  Asynchronous: returns once the work is
+ * enqueued. */
+int inpaint_best_patch_noalloc(const uint8_t* d_rgb, const uint8_t* d_mask, int width, int height,
+                               int patch_radius, int px, int py, uint64_t* d_best_key,
+                               void* cuda_stream);
+
 /* Releases the context and all its device memory (after synchronising its
  * stream).  NULL is a no-op. */
 void inpaint_destroy(inpaint_ctx* ctx);

@@ -138,6 +138,7 @@ SIGNATURES = {
     "inpaint_status_str": (ctypes.c_char_p, [_I]),
     "inpaint_last_error": (ctypes.c_char_p, []),
     "inpaint_probe_peaks": (_I, [ctypes.POINTER(Peaks)]),
+    "inpaint_best_patch_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "inpaint_loop_timing": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(_I)]),
 }

@@ -387,6 +387,8 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
 
 }  // namespace
 
+void inp::set_last_error(const char* msg) { g_last_error = msg; }
+
 // Per-device table of the data term D = (dot / sqrt(nn)) / 510 (Eq. 2 with
 // alpha = 255 and the factor 2 of the central difference), evaluated with
 // the same IEEE double operations the kernels would use (sqrt and division

@@ -327,6 +327,7 @@ __device__ inline void warp_select(const ImgState& s) {
 }
 
 // ---- host-side launchers (defined in the .cu files) ----
+void set_last_error(const char* msg);  // text returned by inpaint_last_error()
 cudaError_t launch_init(const ImgState& s, const uint8_t* rgb, int rgb_stride, const uint8_t* mask,
                         int mask_stride, int32_t* sat, int* omega_count, cudaStream_t st);
 cudaError_t launch_import(const ImgState& s, const uint8_t* rgb, const uint8_t* omega,
