@@ -24,8 +24,8 @@ LIB_PATH = os.path.join(OUT_DIR, "libinpaint.so")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [
-    ARCH, "-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",
-    "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC,
+    ARCH, "-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-rdc=true", "-maxrregcount=128",
+    "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC,
 ]
 
 _lock = threading.Lock()
@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, ARCH, "-rdc=true", "-shared", "-o", tmp, *objs]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")

@@ -8,7 +8,7 @@
 
 namespace inp {
 
-static const EngineFns* fns(int r) {
+const EngineFns* engine_fns(int r) {
   switch (r) {
     case 1: return engine_fns_r1();
     case 2: return engine_fns_r2();
@@ -22,24 +22,14 @@ static const EngineFns* fns(int r) {
   }
 }
 
-cudaError_t engine_occupancy(int r, int srw, int* blocks_per_sm) {
-  const EngineFns* f = fns(r);
-  return f ? f->occupancy(srw, blocks_per_sm) : cudaErrorInvalidValue;
-}
-
-cudaError_t engine_launch(int r, int srw, const EngineArgs& ea, int grid, cudaStream_t st) {
-  const EngineFns* f = fns(r);
-  return f ? f->launch(srw, ea, grid, st) : cudaErrorInvalidValue;
-}
-
 cudaError_t launch_update_fast(const ImgState& s, unsigned long long cond, int use_cond,
                                cudaStream_t st) {
-  const EngineFns* f = fns(s.r);
+  const EngineFns* f = engine_fns(s.r);
   return f ? f->update_fast(s, cond, use_cond, st) : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_prio_init_fast(const ImgState& s, cudaStream_t st) {
-  const EngineFns* f = fns(s.r);
+  const EngineFns* f = engine_fns(s.r);
   return f ? f->prio_init(s, st) : cudaErrorInvalidValue;
 }
 

@@ -93,6 +93,7 @@ struct EngGeom {
   static constexpr int BH = B + 2 * R;               // staged rows
   static constexpr int STAGE_BYTES = ((BW * BH * 4 + 127) / 128) * 128;
   static constexpr int NROW = (4 + P - 1 + 3) & ~3;  // strip words per lane
+  static constexpr int TP = (P + 3) & ~3;            // padded target row (words)
   static constexpr unsigned FULL = (1u << P) - 1u;
 };
 
@@ -111,7 +112,7 @@ __device__ inline void compute_rows(const uint32_t* __restrict__ stage, int row0
   for (int o = 0; o < SRW; ++o)
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[o][k] = 0;
-#pragma unroll 1
+#pragma unroll
   for (int sr = 0; sr < SRW + 2 * R; ++sr) {
     uint32_t row[NROW];
     const uint4* sp = reinterpret_cast<const uint4*>(stage + (row0 + sr) * BW + lane * 4);
@@ -129,14 +130,22 @@ __device__ inline void compute_rows(const uint32_t* __restrict__ stage, int row0
       if (dy < 0 || dy >= P) continue;
       const uint32_t m = rowmask[dy];
       if (m == 0) continue;
-      const uint32_t* trow = tgt + dy * P;
+      uint32_t t[G::TP];
+      const uint4* tp = reinterpret_cast<const uint4*>(tgt + dy * G::TP);
+#pragma unroll
+      for (int i = 0; i < G::TP / 4; ++i) {
+        const uint4 v = tp[i];
+        t[4 * i] = v.x;
+        t[4 * i + 1] = v.y;
+        t[4 * i + 2] = v.z;
+        t[4 * i + 3] = v.w;
+      }
       if (m == G::FULL) {
 #pragma unroll
         for (int dx = 0; dx < P; ++dx) {
-          const uint32_t a = trow[dx];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const uint32_t d = __vabsdiffu4(a, row[k + dx]);
+            const uint32_t d = __vabsdiffu4(t[dx], row[k + dx]);
             acc[o][k] = __dp4a(d, d, acc[o][k]);
           }
         }
@@ -144,10 +153,9 @@ __device__ inline void compute_rows(const uint32_t* __restrict__ stage, int row0
 #pragma unroll
         for (int dx = 0; dx < P; ++dx) {
           if (m & (1u << dx)) {
-            const uint32_t a = trow[dx];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              const uint32_t d = __vabsdiffu4(a, row[k + dx]);
+              const uint32_t d = __vabsdiffu4(t[dx], row[k + dx]);
               acc[o][k] = __dp4a(d, d, acc[o][k]);
             }
           }
@@ -165,10 +173,12 @@ struct EngSmemTail {
   int red32[32];
   int flag;
   int stop;
+  int px, py;
+  uint8_t known[17 * 17];
 };
 
-constexpr int kTgtWords = 17 * 17 + 17 + 3;  // target words + row masks (R <= 8)
-constexpr size_t kHeadBytes = ((sizeof(EngSmemTail) + kTgtWords * 4 + 127) / 128) * 128;
+constexpr int kTgtWords = 17 * 20 + 17 + 3;  // padded target rows + row masks (R <= 8)
+constexpr size_t kHeadBytes = ((((sizeof(EngSmemTail) + 15) & ~size_t(15)) + kTgtWords * 4 + 127) / 128) * 128;
 
 template <int R, int SRW>
 __host__ __device__ constexpr size_t eng_smem_bytes() {
@@ -178,120 +188,190 @@ __host__ __device__ constexpr size_t eng_smem_bytes() {
   return kHeadBytes + (srch > upd ? srch : upd) + 128;
 }
 
-// Bounded wait until the team epoch moves past `epoch` (thread 0 only).
-__device__ inline void wait_epoch(TeamCtl* tc, unsigned epoch, int* err, unsigned long long limit) {
+// Team publication word: epoch (bits 0-31), next target px (32-46), py
+// (47-61), stop flag (62).  One acquire load gives a waiting CTA everything
+// it needs to start the next search round.
+__device__ inline unsigned long long pub_pack(unsigned epoch, int px, int py, bool stop) {
+  return (unsigned long long)epoch | ((unsigned long long)(px & 0x7fff) << 32) |
+         ((unsigned long long)(py & 0x7fff) << 47) | ((unsigned long long)(stop ? 1 : 0) << 62);
+}
+
+__device__ inline unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ inline void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ inline void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait (thread 0) for a publication with an epoch other than `epoch`;
+// returns it, or a stop word after setting *err on timeout.
+__device__ inline unsigned long long wait_pub(TeamCtl* tc, unsigned epoch, int* err,
+                                              unsigned long long limit) {
+  unsigned long long v = ld_acquire64(&tc->pub);
+  if ((unsigned)v != epoch) return v;
   const unsigned long long t0 = globaltimer();
-  while (ld_acquire(&tc->epoch) == epoch) {
+  while (true) {
+    __nanosleep(20);
+    v = ld_acquire64(&tc->pub);
+    if ((unsigned)v != epoch) return v;
     if (globaltimer() - t0 > limit) {
       atomicExch(err, INPAINT_ERR_TIMEOUT);
-      return;
+      return pub_pack(epoch + 1u, 0, 0, true);
     }
-    __nanosleep(64);
   }
 }
 
+// Bounded wait (thread 0) until `n` searchers arrived; false on timeout.
+__device__ inline bool wait_arrivals(TeamCtl* tc, unsigned n, int* err, unsigned long long limit) {
+  if (ld_acquire(&tc->arrive) >= n) return true;
+  const unsigned long long t0 = globaltimer();
+  while (ld_acquire(&tc->arrive) < n) {
+    if (globaltimer() - t0 > limit) {
+      atomicExch(err, INPAINT_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ inline bool ctrl_active(const Ctrl* c) {
+  return __ldcg(&c->status) == 0 && __ldcg(&c->remaining) > 0 &&
+         __ldcg(&c->iter) < __ldcg(&c->iter_limit);
+}
+
+// Roles of a team on one image: CTAs [0, ns) search; the last CTA (the
+// leader) runs the speculative phase of each iteration while they search,
+// waits for them, applies the update and publishes the next round; any other
+// CTA idles until the image is done.  A team of one CTA does all of it in
+// sequence.
+// Per-image part of the engine: the fill loop of image j for this CTA's
+// team (roles below).  Called by k_engine (engine_multi.cu) through
+// run_image_r<R>_s<SRW>, once per image of the team's list.
 template <int R, int SRW>
-__global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
+__device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x) {
   using G = EngGeom<R, SRW>;
   constexpr int P = G::P, B = G::B;
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint8_t* smem = x.smem;
   EngSmemTail& tl = *reinterpret_cast<EngSmemTail*>(smem);
-  uint32_t* tgt = reinterpret_cast<uint32_t*>(smem + sizeof(EngSmemTail));
-  uint32_t* rowmask = tgt + P * P;
+  uint32_t* tgt = reinterpret_cast<uint32_t*>(smem + ((sizeof(EngSmemTail) + 15) & ~size_t(15)));
+  uint32_t* rowmask = tgt + P * G::TP;
   uint8_t* big = smem + kHeadBytes;
   uint32_t* stage0 = reinterpret_cast<uint32_t*>(big);
   uint32_t* stage1 = reinterpret_cast<uint32_t*>(big + G::STAGE_BYTES);
   UpdSmem<R>& usm = *reinterpret_cast<UpdSmem<R>*>(big);
-
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int cta = blockIdx.x;
-  const int team = ea.cta_team[cta];
-  const int first = ea.team_first[team];
-  const int rank = cta - first, tsize = ea.team_first[team + 1] - first;
-  TeamCtl* tc = &ea.teams[team];
-  unsigned long long* tpart = ea.partials + first;
+  const int rank = x.rank, tsize = x.tsize;
+  TeamCtl* tc = x.tc;
+  unsigned long long* tpart = x.tpart;
   const unsigned long long limit = ea.wait_limit_ns;
-
-  if (tid == 0) {
-    mbar_init(&tl.full[0], 1);
-    mbar_init(&tl.full[1], 1);
-  }
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  __syncthreads();
-  uint32_t ph0 = 0, ph1 = 0;
-  unsigned epoch = ld_acquire(&tc->epoch);
-  unsigned long long t_prev = globaltimer();
-
-  for (int li = ea.team_img_off[team]; li < ea.team_img_off[team + 1]; ++li) {
-    const int j = ea.team_img[li];
+  uint32_t ph0 = x.ph0, ph1 = x.ph1;
+  unsigned epoch = x.epoch;
+  bool resident = false;  // stage0 holds this CTA's only batch of the image
+  {
     const ImgState s = ea.imgs[j];
     const CUtensorMap* map = &ea.tmaps[j];
     Ctrl* c = s.ctrl;
-    // candidate batches: B rows x 128 columns; the column grid is aligned so
-    // that every TMA x coordinate is a multiple of 4 words
     const int xb = R + ((s.cx0 - R) & ~3);
-    const int ncg = (s.cx1 - xb + 128) / 128;
-    const int nrb = (s.cy1 - s.cy0 + B) / B;
+    const int ncg = s.cx1 >= s.cx0 ? (s.cx1 - xb + 128) / 128 : 0;
+    const int nrb = s.cy1 >= s.cy0 ? (s.cy1 - s.cy0 + B) / B : 0;
     const int nbatch = ncg * nrb;
-    // roles: searchers [0, ns), one speculative-phase CTA (the last rank),
-    // the rest idle for this image; a team of one does everything itself
     const int ns = tsize >= 2 ? min(tsize - 1, nbatch) : 1;
-    const bool spec_cta = tsize >= 2 ? rank == tsize - 1 : true;
+    const bool leader = tsize >= 2 ? rank == tsize - 1 : true;
     const bool searcher = rank < ns;
-    const unsigned n_arrive = tsize >= 2 ? (unsigned)ns + 1u : 1u;
-    const bool idle = !searcher && !spec_cta;
-    while (true) {
-      if (tid == 0) {
-        tl.stop = !(__ldcg(&c->status) == 0 && __ldcg(&c->remaining) > 0 &&
-                    __ldcg(&c->iter) < __ldcg(&c->iter_limit)) ||
-                  __ldcg(ea.err) != 0;
-      }
-      __syncthreads();
-      if (tl.stop) break;
-      if (idle) {
-        if (tid == 0) wait_epoch(tc, epoch, ea.err, limit);
-        ++epoch;
-        __syncthreads();
-        continue;
-      }
-      unsigned long long best = ~0ull;
-      if (spec_cta) {
+    resident = false;
+    // state at the start of this image (written before the launch or by the
+    // previous image's last update, both visible here)
+    if (tid == 0) {
+      tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
+      tl.px = __ldcg(&c->px);
+      tl.py = __ldcg(&c->py);
+    }
+    __syncthreads();
+    int prev_px = -1000000, prev_py = -1000000;
+    while (!tl.stop) {
+      const int px = tl.px, py = tl.py;
+      if (leader) {
+        const unsigned long long t_a = globaltimer();
         spec_phase<R>(s, usm);
-        __threadfence();
         __syncthreads();
+        if (tid == 0) tl.flag = wait_arrivals(tc, (unsigned)(tsize >= 2 ? ns : 0), ea.err, limit);
+        __syncthreads();
+        if (tsize >= 2) {
+          bool stop = true;
+          int npx = 0, npy = 0;
+          if (tl.flag) {
+            const unsigned long long t_b = globaltimer();
+            update_phase<R>(s, tpart, ns, usm);
+            __syncthreads();
+            stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
+            npx = __ldcg(&c->px);
+            npy = __ldcg(&c->py);
+            if (tid == 0) {
+              const unsigned long long t_c = globaltimer();
+              c->t_search += t_b - t_a;
+              c->t_update += t_c - t_b;
+              c->timed_iters += 1;
+            }
+          }
+          __syncthreads();
+          if (tid == 0) {
+            tc->arrive = 0u;
+            st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
+            tl.stop = stop;
+            tl.px = npx;
+            tl.py = npy;
+          }
+          ++epoch;
+          __syncthreads();
+          continue;
+        }
       }
       if (searcher) {
-        const int px = __ldcg(&c->px), py = __ldcg(&c->py);
-        if (tid < P) {  // target patch: known in-image pixels and per-row bit masks
-          const int ty = py + tid - R;
-          uint32_t m = 0;
-          for (int dx = 0; dx < P; ++dx) {
-            const int tx = px + dx - R;
-            uint32_t w = 0;
-            if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H &&
-                __ldcg(&s.omega[(size_t)ty * s.W + tx]) == 0) {
-              w = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
-              m |= 1u << dx;
-            }
-            tgt[tid * P + dx] = w;
-          }
-          rowmask[tid] = m;
-        }
+        // first batch: reuse the resident tile unless the last fill touched it
+        const int b0 = rank;
+        const bool need0 = !resident ||
+                           (abs(prev_px - (xb + 128 * (b0 % ncg) + 64)) <= 64 + 2 * R + 4 &&
+                            abs(prev_py - (s.cy0 + B * (b0 / ncg) + B / 2)) <= B / 2 + 2 * R + 1);
         auto issue = [&](int b, uint32_t* st, uint64_t* bar) {
           const int gx = b % ncg, gy = b / ncg;
           asm volatile("fence.proxy.async;" ::: "memory");
           mbar_expect_tx(bar, (uint32_t)(G::BW * G::BH * 4));
           tma_load_2d(st, map, xb - R + 128 * gx, s.cy0 + B * gy - R, bar);
         };
-        if (tid == 0 && rank < nbatch) issue(rank, stage0, &tl.full[0]);
-        __syncthreads();  // target ready
+        if (tid == 0 && b0 < nbatch && need0) issue(b0, stage0, &tl.full[0]);
+        // target patch: one thread per pixel, then the row masks
+        if (tid < P * P) {
+          const int tx = px + tid % P - R, ty = py + tid / P - R;
+          uint32_t w = 0;
+          int known = 0;
+          if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H &&
+              __ldcg(&s.omega[(size_t)ty * s.W + tx]) == 0) {
+            w = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
+            known = 1;
+          }
+          tgt[(tid / P) * G::TP + tid % P] = w;
+          tl.known[tid] = (uint8_t)known;
+        }
+        __syncthreads();
+        if (tid < P) {
+          uint32_t m = 0;
+          for (int dx = 0; dx < P; ++dx) m |= (uint32_t)tl.known[tid * P + dx] << dx;
+          rowmask[tid] = m;
+        }
+        __syncthreads();
+        unsigned long long best = ~0ull;
         int cur = 0;
         bool ok = true;
-        for (int b = rank; b < nbatch; b += ns) {
+        for (int b = b0; b < nbatch; b += ns) {
           const int nb = b + ns;
           if (tid == 0 && nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1]);
-          // validity of this lane's candidates, loaded while the tile arrives
           const int gx = b % ncg, gy = b / ncg;
           const int qx0 = xb + 128 * gx + lane * 4, qy0 = s.cy0 + B * gy + warp * SRW;
           int cnt[SRW][4];
@@ -304,8 +384,11 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
                               ? __ldcg(&s.count[(size_t)qy * s.W + qx])
                               : 1;
             }
-          const bool got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
-          if (cur) ph1 ^= 1; else ph0 ^= 1;
+          bool got = true;
+          if (b != b0 || need0) {
+            got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
+            if (cur) ph1 ^= 1; else ph0 ^= 1;
+          }
           uint32_t acc[SRW][4];
           compute_rows<R, SRW>(cur ? stage1 : stage0, warp * SRW, tgt, rowmask, acc);
 #pragma unroll
@@ -317,8 +400,6 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
                 const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
                 best = key < best ? key : best;
               }
-          // every warp is done with this stage; a bounded wait that gave up
-          // anywhere ends the search uniformly (after the prefetch landed)
           if (__syncthreads_or(!got)) {
             ok = false;
             if (nb < nbatch) {
@@ -329,66 +410,60 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
           }
           cur ^= 1;
         }
+        // the tile stays resident when it is this CTA's only batch
+        resident = ok && tsize >= 2 && b0 + ns >= nbatch && b0 < nbatch;
         if (!ok && tid == 0) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
         best = block_min_u64(best, tl.red64);
-      }
-
-      // arrive; the last arrival applies the iteration
-      if (tid == 0) {
-        if (searcher) tpart[rank] = best;
-        __threadfence();
-        const unsigned old = atomicAdd(&tc->arrive, 1u);
-        tl.flag = (old == n_arrive - 1u);
-      }
-      __syncthreads();
-      if (tl.flag) {
-        __threadfence();
-        const unsigned long long t_a = globaltimer();
-        update_phase<R>(s, tpart, ns, usm);
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-          const unsigned long long t_b = globaltimer();
-          c->t_search += t_a - t_prev;
-          c->t_update += t_b - t_a;
-          c->t_last = t_b;
-          c->timed_iters += 1;
-          tc->arrive = 0u;
+        if (tsize == 1) {
+          // team of one: apply the iteration right away
+          if (tid == 0) tpart[0] = best;
           __threadfence();
-          st_release(&tc->epoch, epoch + 1u);
+          __syncthreads();
+          const unsigned long long t_b = globaltimer();
+          update_phase<R>(s, tpart, 1, usm);
+          __syncthreads();
+          if (tid == 0) {
+            c->t_update += globaltimer() - t_b;
+            c->timed_iters += 1;
+            tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
+            tl.px = __ldcg(&c->px);
+            tl.py = __ldcg(&c->py);
+          }
+          resident = false;
+          prev_px = px;
+          prev_py = py;
+          __syncthreads();
+          continue;
         }
-      } else if (tid == 0) {
-        wait_epoch(tc, epoch, ea.err, limit);
+        if (tid == 0) {
+          tpart[rank] = best;
+          red_release_add(&tc->arrive, 1u);
+        }
+      }
+      // searchers and idle CTAs: wait for the next round
+      if (tid == 0) {
+        const unsigned long long v = wait_pub(tc, epoch, ea.err, limit);
+        tl.stop = ((v >> 62) & 1ull) != 0;
+        tl.px = (int)((v >> 32) & 0x7fff);
+        tl.py = (int)((v >> 47) & 0x7fff);
       }
       ++epoch;
+      prev_px = px;
+      prev_py = py;
       __syncthreads();
-      t_prev = __ldcg(&c->t_last);
+      if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
     }
   }
+  x.ph0 = ph0;
+  x.ph1 = ph1;
+  x.epoch = epoch;
 }
 
-// ---------------------------------------------------------------- host side
-
+// Shared-memory bytes the engine needs for radius R and SRW rows per warp.
 template <int R, int SRW>
-static cudaError_t launch_t(const EngineArgs& ea, int grid, cudaStream_t st) {
-  const size_t smem = eng_smem_bytes<R, SRW>();
-  cudaError_t e = cudaFuncSetAttribute(k_engine<R, SRW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  void* args[] = {const_cast<EngineArgs*>(&ea)};
-  return cudaLaunchCooperativeKernel((const void*)k_engine<R, SRW>, dim3(grid), dim3(kEngThreads),
-                                     args, smem, st);
+constexpr size_t engine_smem_for() {
+  return eng_smem_bytes<R, SRW>();
 }
-
-template <int R, int SRW>
-static cudaError_t occupancy_t(int* blocks) {
-  const size_t smem = eng_smem_bytes<R, SRW>();
-  cudaError_t e = cudaFuncSetAttribute(k_engine<R, SRW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_engine<R, SRW>, kEngThreads, smem);
-}
-
 
 }  // namespace inp
 
@@ -444,18 +519,14 @@ static cudaError_t prio_init_t(const ImgState& s, cudaStream_t st) {
 
 namespace inp {
 
-// Entry points of one radius R, exported through EngineFns.
+// Host entry points of one radius R, exported through EngineFns.
 template <int R>
-static cudaError_t eng_launch_r(int srw, const EngineArgs& ea, int grid, cudaStream_t st) {
-  return srw == 2 ? launch_t<R, 2>(ea, grid, st) : launch_t<R, 1>(ea, grid, st);
-}
-template <int R>
-static cudaError_t eng_occ_r(int srw, int* blocks) {
-  return srw == 2 ? occupancy_t<R, 2>(blocks) : occupancy_t<R, 1>(blocks);
+static size_t eng_smem_r(int srw) {
+  return srw == 2 ? engine_smem_for<R, 2>() : engine_smem_for<R, 1>();
 }
 template <int R>
 const EngineFns* engine_fns_for() {
-  static const EngineFns f = {eng_launch_r<R>, eng_occ_r<R>, upd_fast_t<R>, prio_init_t<R>};
+  static const EngineFns f = {eng_smem_r<R>, upd_fast_t<R>, prio_init_t<R>};
   return &f;
 }
 

@@ -1,0 +1,77 @@
+// The persistent engine kernel: one cooperative launch runs the fill loops
+// of every image of every team to completion (single image: one team of all
+// CTAs; batch: many teams, each with a list of images).  The per-image body
+// for the image's patch radius is selected at run time.
+#include "inpaint_engine.h"
+
+namespace inp {
+
+__device__ inline unsigned long long ld_acquire64_pub(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int SRW>
+__device__ inline void run_by_radius(const EngineArgs& ea, int j, EngCtx& x) {
+  switch (ea.imgs[j].r) {
+#define INP_CASE(R)                                  \
+  case R:                                            \
+    if (SRW == 1) run_image_r##R##_s1(ea, j, x);     \
+    else run_image_r##R##_s2(ea, j, x);              \
+    break;
+    INP_CASE(1) INP_CASE(2) INP_CASE(3) INP_CASE(4) INP_CASE(5) INP_CASE(6) INP_CASE(7)
+    INP_CASE(8)
+#undef INP_CASE
+    default:
+      break;
+  }
+}
+
+template <int SRW>
+__global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  EngCtx x;
+  x.smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const int team = ea.cta_team[blockIdx.x];
+  const int first = ea.team_first[team];
+  x.rank = blockIdx.x - first;
+  x.tsize = ea.team_first[team + 1] - first;
+  x.tc = &ea.teams[team];
+  x.tpart = ea.partials + first;
+  // the two TMA completion barriers sit at the start of shared memory
+  uint64_t* bars = reinterpret_cast<uint64_t*>(x.smem);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bars[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bars[1])) : "memory");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  x.ph0 = 0;
+  x.ph1 = 0;
+  x.epoch = (unsigned)ld_acquire64_pub(&x.tc->pub);
+  for (int li = ea.team_img_off[team]; li < ea.team_img_off[team + 1]; ++li)
+    run_by_radius<SRW>(ea, ea.team_img[li], x);
+}
+
+template <int SRW>
+static cudaError_t set_smem(size_t smem) {
+  return cudaFuncSetAttribute(k_engine<SRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t engine_occupancy(int srw, size_t smem, int* blocks_per_sm) {
+  cudaError_t e = srw == 2 ? set_smem<2>(smem) : set_smem<1>(smem);
+  if (e != cudaSuccess) return e;
+  return srw == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine<2>, kEngThreads, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine<1>, kEngThreads, smem);
+}
+
+cudaError_t engine_launch(int srw, size_t smem, const EngineArgs& ea, int grid, cudaStream_t st) {
+  cudaError_t e = srw == 2 ? set_smem<2>(smem) : set_smem<1>(smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<EngineArgs*>(&ea)};
+  const void* fn = srw == 2 ? (const void*)k_engine<2> : (const void*)k_engine<1>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kEngThreads), args, smem, st);
+}
+
+}  // namespace inp

@@ -1,7 +1,9 @@
-// Persistent engine, fast update and priority-init kernels for patch radius 4
-// (one translation unit per radius so that the instantiations build in parallel).
+// Persistent engine body, fast update and priority-init kernels for patch
+// radius 4 (one translation unit per radius so that they build in parallel).
 #include "engine_impl.cuh"
 
 namespace inp {
+__device__ void run_image_r4_s1(const EngineArgs& ea, int j, EngCtx& x) { run_image<4, 1>(ea, j, x); }
+__device__ void run_image_r4_s2(const EngineArgs& ea, int j, EngCtx& x) { run_image<4, 2>(ea, j, x); }
 const EngineFns* engine_fns_r4() { return engine_fns_for<4>(); }
 }  // namespace inp

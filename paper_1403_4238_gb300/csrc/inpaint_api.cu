@@ -59,6 +59,7 @@ struct inpaint_ctx {
   // persistent engine (one team of every CTA)
   bool eng_ready = false;
   int eng_grid = 0, eng_sr = 0;
+  size_t eng_smem = 0;
   EngineArgs ea{};
   ImgState* d_img = nullptr;
   CUtensorMap* d_tmap = nullptr;
@@ -197,15 +198,18 @@ int setup_engine(inpaint_ctx* c) {
     g_last_error = "tile_rows must be 0, 1 or 2";
     return INPAINT_ERR_ARG;
   }
+  const EngineFns* f = engine_fns(c->r);
+  if (!f) return INPAINT_ERR_UNSUPPORTED;
   int bps = 0;
-  CK(engine_occupancy(c->r, sr ? sr : 2, &bps));
+  CK(engine_occupancy(sr ? sr : 2, f->smem_bytes(sr ? sr : 2), &bps));
   if (bps < 1) {
     g_last_error = "engine kernel does not fit on an SM";
     return INPAINT_ERR_UNSUPPORTED;
   }
   const int grid = sms * bps;
   if (!sr) sr = pick_rows_per_warp(c->st, grid);
-  CK(engine_occupancy(c->r, sr, &bps));
+  c->eng_smem = f->smem_bytes(sr);
+  CK(engine_occupancy(sr, c->eng_smem, &bps));
   const int g2 = sms * (bps < 1 ? 1 : bps);
   c->eng_grid = g2 < grid ? g2 : grid;
   c->eng_sr = sr;
@@ -250,7 +254,7 @@ int run_engine(inpaint_ctx* c) {
   if (rc) return rc;
   CK(cudaMemsetAsync(c->d_team, 0, sizeof(TeamCtl), c->stream));
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-  CK(engine_launch(c->r, c->eng_sr, c->ea, c->eng_grid, c->stream));
+  CK(engine_launch(c->eng_sr, c->eng_smem, c->ea, c->eng_grid, c->stream));
   CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   return INPAINT_OK;
 }

@@ -12,9 +12,9 @@ constexpr int kEngWarps = kEngThreads / 32;
 
 // Per-team synchronisation words (global memory).
 struct TeamCtl {
-  unsigned epoch;   // iterations completed by the team (release-published)
-  unsigned arrive;  // members arrived in the current iteration
-  unsigned pad[30]; // keep teams on separate 128-byte lines
+  unsigned long long pub;  // epoch | next px | next py | stop (release-published)
+  unsigned arrive;         // searchers arrived in the current iteration
+  unsigned pad[29];        // keep teams on separate 128-byte lines
 };
 
 struct EngineArgs {
@@ -30,10 +30,34 @@ struct EngineArgs {
   unsigned long long wait_limit_ns;
 };
 
-// Kernels of one patch radius (engine_r<R>.cu).
+// Per-CTA engine state carried from one image of a team's list to the next.
+struct EngCtx {
+  uint8_t* smem;                // dynamic shared memory, 128-byte aligned
+  int rank, tsize;              // this CTA's rank in its team, team size
+  TeamCtl* tc;
+  unsigned long long* tpart;    // partial keys of the team's CTAs
+  uint32_t ph0, ph1;            // phase parities of the two TMA barriers
+  unsigned epoch;               // team publications seen
+};
+
+// Per-image engine body for radius R and SRW rows per warp (engine_r<R>.cu),
+// called from the one engine kernel (engine_multi.cu) by the image's radius.
+#define INP_DECL_RUN_IMAGE(R)                                            \
+  __device__ void run_image_r##R##_s1(const EngineArgs& ea, int j, EngCtx& x); \
+  __device__ void run_image_r##R##_s2(const EngineArgs& ea, int j, EngCtx& x);
+INP_DECL_RUN_IMAGE(1)
+INP_DECL_RUN_IMAGE(2)
+INP_DECL_RUN_IMAGE(3)
+INP_DECL_RUN_IMAGE(4)
+INP_DECL_RUN_IMAGE(5)
+INP_DECL_RUN_IMAGE(6)
+INP_DECL_RUN_IMAGE(7)
+INP_DECL_RUN_IMAGE(8)
+#undef INP_DECL_RUN_IMAGE
+
+// Host-side entry points of one patch radius (engine_r<R>.cu).
 struct EngineFns {
-  cudaError_t (*launch)(int srw, const EngineArgs& ea, int grid, cudaStream_t st);
-  cudaError_t (*occupancy)(int srw, int* blocks_per_sm);
+  size_t (*smem_bytes)(int srw);  // dynamic shared memory of the engine for this radius
   cudaError_t (*update_fast)(const ImgState& s, unsigned long long cond, int use_cond,
                              cudaStream_t st);
   cudaError_t (*prio_init)(const ImgState& s, cudaStream_t st);
@@ -47,8 +71,11 @@ const EngineFns* engine_fns_r6();
 const EngineFns* engine_fns_r7();
 const EngineFns* engine_fns_r8();
 
-cudaError_t engine_occupancy(int r, int sr, int* blocks_per_sm);
-cudaError_t engine_launch(int r, int sr, const EngineArgs& ea, int grid, cudaStream_t st);
+const EngineFns* engine_fns(int r);
+// Engine kernel (engine_multi.cu) for SRW rows per warp; smem = the largest
+// engine_fns(r)->smem_bytes(srw) over the radii of the images in the launch.
+cudaError_t engine_occupancy(int srw, size_t smem, int* blocks_per_sm);
+cudaError_t engine_launch(int srw, size_t smem, const EngineArgs& ea, int grid, cudaStream_t st);
 int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out);
 cudaError_t launch_update_fast(const ImgState& s, unsigned long long cond, int use_cond,
                                cudaStream_t st);

@@ -229,22 +229,28 @@ __device__ inline int block_sum_int(int v, int* scratch) {
 
 // ---- priority tiles: two-level argmax structure over the prio keys ----
 
-// Rescans level-0 tile (tx, ty) from the pixel keys; one warp.
+// Rescans level-0 tile (tx, ty) from the pixel keys; one warp.  The eight
+// loads of a lane are issued together (unrolled), then compared.
 __device__ inline void warp_rescan_t0(const ImgState& s, int tx, int ty) {
   const int lane = threadIdx.x & 31;
+  constexpr int N = kT0 * kT0 / 32;
+  unsigned long long kk[N];
+  int ii[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    const int j = lane + 32 * t;
+    const int x = tx * kT0 + (j & (kT0 - 1)), y = ty * kT0 + j / kT0;
+    ii[t] = y * s.W + x;
+    kk[t] = (x < s.W && y < s.H) ? __ldcg(&s.prio[ii[t]]) : 0ull;
+  }
   unsigned long long k = 0ull;
   int idx = 0x7fffffff;
-  for (int j = lane; j < kT0 * kT0; j += 32) {
-    const int x = tx * kT0 + (j & (kT0 - 1)), y = ty * kT0 + j / kT0;
-    if (x < s.W && y < s.H) {
-      const int i = y * s.W + x;
-      const unsigned long long kk = __ldcg(&s.prio[i]);
-      if (prio_better(kk, i, k, idx)) {
-        k = kk;
-        idx = i;
-      }
+#pragma unroll
+  for (int t = 0; t < N; ++t)
+    if (prio_better(kk[t], ii[t], k, idx)) {
+      k = kk[t];
+      idx = ii[t];
     }
-  }
   warp_best_prio(k, idx);
   if (lane == 0) {
     s.tiles0[ty * s.t0x + tx].key = k;
@@ -255,19 +261,28 @@ __device__ inline void warp_rescan_t0(const ImgState& s, int tx, int ty) {
 // Rescans level-1 tile (ux, uy) from the level-0 entries; one warp.
 __device__ inline void warp_rescan_t1(const ImgState& s, int ux, int uy) {
   const int lane = threadIdx.x & 31;
-  unsigned long long k = 0ull;
-  int idx = 0x7fffffff;
-  for (int j = lane; j < kT1 * kT1; j += 32) {
+  constexpr int N = kT1 * kT1 / 32;
+  unsigned long long kk[N];
+  int ii[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    const int j = lane + 32 * t;
     const int tx = ux * kT1 + (j & (kT1 - 1)), ty = uy * kT1 + j / kT1;
+    kk[t] = 0ull;
+    ii[t] = 0x7fffffff;
     if (tx < s.t0x && ty < s.t0y) {
-      const unsigned long long bk = __ldcg(&s.tiles0[ty * s.t0x + tx].key);
-      const int bi = __ldcg(&s.tiles0[ty * s.t0x + tx].idx);
-      if (prio_better(bk, bi, k, idx)) {
-        k = bk;
-        idx = bi;
-      }
+      kk[t] = __ldcg(&s.tiles0[ty * s.t0x + tx].key);
+      ii[t] = __ldcg(&s.tiles0[ty * s.t0x + tx].idx);
     }
   }
+  unsigned long long k = 0ull;
+  int idx = 0x7fffffff;
+#pragma unroll
+  for (int t = 0; t < N; ++t)
+    if (prio_better(kk[t], ii[t], k, idx)) {
+      k = kk[t];
+      idx = ii[t];
+    }
   warp_best_prio(k, idx);
   if (lane == 0) {
     s.tiles1[uy * s.t1x + ux].key = k;
