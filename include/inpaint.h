@@ -86,6 +86,10 @@ typedef struct {
   int tile_rows;         /* engine search: candidate rows per warp in a search batch
                             (a batch is 16 warps x rows x 128 candidate columns):
                             1 or 2; 0 = chosen by the library */
+  const char* tuning_file; /* NULL, or a text table written by the autotuner: one line
+                            "radius max_pixels rows_per_warp" per bucket; the first
+                            line with the image's radius and W*H <= max_pixels
+                            gives rows_per_warp when tile_rows is 0 */
 } inpaint_options;
 
 #define INPAINT_LOOP_AUTO 0
@@ -212,6 +216,55 @@ int inpaint_search_rect(const inpaint_ctx* ctx, int* x0, int* x1, int* y0, int* 
 int inpaint_best_patch_noalloc(const uint8_t* d_rgb, const uint8_t* d_mask, int width, int height,
                                int patch_radius, int px, int py, uint64_t* d_best_key,
                                void* cuda_stream);
+
+/* ---- Batched form: many independent images in one persistent launch ----
+ * Every image runs the same fill loop as inpaint_run, bit for bit; the CTAs
+ * of one cooperative launch are split into teams, each team running the loop
+ * of its images one after the other (team sizes proportional to each image's
+ * estimated work; images of any radius 1..8 mix in one launch).  Search
+ * batch heights come from the tuning table (see inpaint_autotune in the
+ * Python package) when opt->tuning_file names one, else from a size rule. */
+typedef struct {
+  const uint8_t* rgb;   /* host, H rows of rgb_stride_bytes, 3 bytes per pixel */
+  int width, height, rgb_stride_bytes;
+  const uint8_t* mask;  /* host, H rows of mask_stride_bytes, nonzero = remove */
+  int mask_stride_bytes;
+  int patch_radius;     /* 1..8 */
+} inpaint_image;
+
+typedef struct inpaint_batch inpaint_batch;
+
+/* Allocates and initialises the device state of n images (inputs are copied;
+ * a device copy of each input is kept for inpaint_batch_reset) and plans the
+ * teams.  opt may be NULL; opt->cuda_stream is used for all work.  Errors as
+ * inpaint_create (INPAINT_ERR_ARG names the first bad image in
+ * inpaint_last_error()). */
+int inpaint_batch_create(const inpaint_image* images, int n, const inpaint_options* opt,
+                         inpaint_batch** out);
+
+/* Re-initialises every image from its kept input (device to device). */
+int inpaint_batch_reset(inpaint_batch* b);
+
+/* Runs every image until its Omega is empty or an error stops it, in one
+ * cooperative kernel launch (iterations limited to max_iters per image when
+ * max_iters > 0).  status_out (nullable, n entries) receives each image's
+ * status (INPAINT_OK, INPAINT_DONE or an error).  Returns INPAINT_OK when
+ * the launch ran (even if some images failed), else an error.
+ * Synchronises the batch's stream. */
+int inpaint_batch_run(inpaint_batch* b, int max_iters, int* status_out);
+
+/* Current image i (RGB, rows of stride_bytes) and its counters; any output
+ * pointer may be NULL. */
+int inpaint_batch_result(const inpaint_batch* b, int i, uint8_t* rgb_out, int stride_bytes,
+                         int* iterations, uint64_t* evals);
+
+/* The launch plan: grid size, number of teams, and per image its team, the
+ * team's size and the search rows per warp.  Arrays may be NULL. */
+int inpaint_batch_plan(const inpaint_batch* b, int* grid, int* n_teams, int* team_of_image,
+                       int* team_size_of_image, int* rows_per_warp);
+
+/* Releases everything (after synchronising the batch's stream). */
+void inpaint_batch_destroy(inpaint_batch* b);
 
 /* Releases the context and all its device memory (after synchronising its
  * stream).  NULL is a no-op. */

@@ -114,6 +114,15 @@ class Options(ctypes.Structure):
         ("form", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("debug_checks", ctypes.c_int),
         ("search_alpha", ctypes.c_double), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p), ("loop_mode", ctypes.c_int), ("tile_rows", ctypes.c_int),
+        ("tuning_file", ctypes.c_char_p),
+    ]
+
+
+class Image(ctypes.Structure):
+    _fields_ = [
+        ("rgb", ctypes.c_void_p), ("width", ctypes.c_int), ("height", ctypes.c_int),
+        ("rgb_stride_bytes", ctypes.c_int), ("mask", ctypes.c_void_p),
+        ("mask_stride_bytes", ctypes.c_int), ("patch_radius", ctypes.c_int),
     ]
 
 
@@ -139,6 +148,12 @@ SIGNATURES = {
     "inpaint_last_error": (ctypes.c_char_p, []),
     "inpaint_probe_peaks": (_I, [ctypes.POINTER(Peaks)]),
     "inpaint_best_patch_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "inpaint_batch_create": (_I, [ctypes.POINTER(Image), _I, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "inpaint_batch_reset": (_I, [_P]),
+    "inpaint_batch_run": (_I, [_P, _I, _P]),
+    "inpaint_batch_result": (_I, [_P, _I, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_uint64)]),
+    "inpaint_batch_plan": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _P, _P]),
+    "inpaint_batch_destroy": (None, [_P]),
     "inpaint_loop_timing": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(_I)]),
 }

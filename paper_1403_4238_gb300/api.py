@@ -209,3 +209,88 @@ def probe_peaks() -> dict:
     pk = _lib.Peaks()
     _check(lib.inpaint_probe_peaks(ctypes.byref(pk)), "inpaint_probe_peaks")
     return {f: getattr(pk, f) for f, _ in _lib.Peaks._fields_}
+
+
+class Batch:
+    """Many independent removals in one persistent launch (inpaint_batch_*).
+
+    cases: iterable of (rgb (H, W, 3) uint8, mask (H, W), patch radius).
+    Results are identical to running each image alone.
+    """
+
+    def __init__(self, cases, *, tile_rows: int = 0, tuning_file: str | None = None, stream=None,
+                 torch_memory: bool = True):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self._alloc = _TorchAllocator(self.device) if torch_memory else None
+        opt = Options()
+        self.lib.inpaint_options_default(ctypes.byref(opt))
+        opt.cuda_stream = self.stream.cuda_stream
+        opt.tile_rows = int(tile_rows)
+        self._tf = tuning_file.encode() if tuning_file else None
+        opt.tuning_file = self._tf
+        if self._alloc is not None:
+            opt.dev_alloc = self._alloc.alloc
+            opt.dev_free = self._alloc.free
+        self._opt = opt
+        self._keep = []
+        imgs = []
+        self.shapes = []
+        for rgb, mask, r in cases:
+            rgb = np.ascontiguousarray(rgb, np.uint8)
+            mask = np.ascontiguousarray(mask, np.uint8)
+            H, W = mask.shape
+            self._keep += [rgb, mask]
+            imgs.append(_lib.Image(rgb.ctypes.data, W, H, 3 * W, mask.ctypes.data, W, int(r)))
+            self.shapes.append((H, W))
+        self.n = len(imgs)
+        arr = (_lib.Image * self.n)(*imgs)
+        b = ctypes.c_void_p()
+        _check(self.lib.inpaint_batch_create(arr, self.n, ctypes.byref(opt), ctypes.byref(b)),
+               "inpaint_batch_create")
+        self.b = b
+        self._keep = []  # inputs were copied
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.inpaint_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self):
+        return _check(self.lib.inpaint_batch_reset(self.b), "inpaint_batch_reset")
+
+    def run(self, max_iters: int = 0):
+        st = (ctypes.c_int * self.n)()
+        _check(self.lib.inpaint_batch_run(self.b, int(max_iters), st), "inpaint_batch_run")
+        return list(st)
+
+    def result(self, i: int):
+        H, W = self.shapes[i]
+        out = np.zeros((H, W, 3), np.uint8)
+        it, ev = ctypes.c_int(), ctypes.c_uint64()
+        _check(self.lib.inpaint_batch_result(self.b, i, out.ctypes.data, 3 * W, ctypes.byref(it),
+                                             ctypes.byref(ev)), "inpaint_batch_result")
+        return out, it.value, ev.value
+
+    def plan(self):
+        g, t = ctypes.c_int(), ctypes.c_int()
+        team = (ctypes.c_int * self.n)()
+        size = (ctypes.c_int * self.n)()
+        rows = (ctypes.c_int * self.n)()
+        _check(self.lib.inpaint_batch_plan(self.b, ctypes.byref(g), ctypes.byref(t), team, size, rows),
+               "inpaint_batch_plan")
+        return dict(grid=g.value, teams=t.value, team=list(team), team_size=list(size), rows=list(rows))

@@ -273,186 +273,176 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   const unsigned long long limit = ea.wait_limit_ns;
   uint32_t ph0 = x.ph0, ph1 = x.ph1;
   unsigned epoch = x.epoch;
+
+  const ImgState s = ea.imgs[j];
+  const CUtensorMap* map = &ea.tmaps[j];
+  Ctrl* c = s.ctrl;
+  const int xb = R + ((s.cx0 - R) & ~3);
+  const int ncg = s.cx1 >= s.cx0 ? (s.cx1 - xb + 128) / 128 : 0;
+  const int nrb = s.cy1 >= s.cy0 ? (s.cy1 - s.cy0 + B) / B : 0;
+  const int nbatch = ncg * nrb;
+  // Roles: CTAs [0, ns) search.  The last CTA of the team is the leader: it
+  // runs the speculative phase of each iteration while the others search,
+  // waits for their keys, applies the update and publishes the next round.
+  // On an image with many batches per CTA the leader searches too; a CTA
+  // that neither searches nor leads idles until the image is done.
+  const bool lead_searches = tsize == 1 || nbatch >= 4 * tsize;
+  const int ns = lead_searches ? tsize : min(tsize - 1, nbatch);
+  const bool leader = rank == tsize - 1;
+  const bool searcher = rank < ns;
+  const unsigned n_wait = (unsigned)(lead_searches ? ns - 1 : ns);
   bool resident = false;  // stage0 holds this CTA's only batch of the image
-  {
-    const ImgState s = ea.imgs[j];
-    const CUtensorMap* map = &ea.tmaps[j];
-    Ctrl* c = s.ctrl;
-    const int xb = R + ((s.cx0 - R) & ~3);
-    const int ncg = s.cx1 >= s.cx0 ? (s.cx1 - xb + 128) / 128 : 0;
-    const int nrb = s.cy1 >= s.cy0 ? (s.cy1 - s.cy0 + B) / B : 0;
-    const int nbatch = ncg * nrb;
-    const int ns = tsize >= 2 ? min(tsize - 1, nbatch) : 1;
-    const bool leader = tsize >= 2 ? rank == tsize - 1 : true;
-    const bool searcher = rank < ns;
-    resident = false;
-    // state at the start of this image (written before the launch or by the
-    // previous image's last update, both visible here)
-    if (tid == 0) {
-      tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
-      tl.px = __ldcg(&c->px);
-      tl.py = __ldcg(&c->py);
+  if (tid == 0) {
+    tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
+    tl.px = __ldcg(&c->px);
+    tl.py = __ldcg(&c->py);
+  }
+  __syncthreads();
+  int prev_px = -1000000, prev_py = -1000000;
+
+  // One search round for target (px, py): this CTA's batches; returns its
+  // best key.  Whole block.
+  auto search_round = [&](int px, int py) -> unsigned long long {
+    const int b0 = rank;
+    const bool need0 = !resident ||
+                       (abs(prev_px - (xb + 128 * (b0 % max(ncg, 1)) + 64)) <= 64 + 2 * R + 4 &&
+                        abs(prev_py - (s.cy0 + B * (b0 / max(ncg, 1)) + B / 2)) <= B / 2 + 2 * R + 1);
+    auto issue = [&](int b, uint32_t* st, uint64_t* bar) {
+      const int gx = b % ncg, gy = b / ncg;
+      asm volatile("fence.proxy.async;" ::: "memory");
+      mbar_expect_tx(bar, (uint32_t)(G::BW * G::BH * 4));
+      tma_load_2d(st, map, xb - R + 128 * gx, s.cy0 + B * gy - R, bar);
+    };
+    if (tid == 0 && b0 < nbatch && need0) issue(b0, stage0, &tl.full[0]);
+    // target patch: one thread per pixel, then the row masks
+    if (tid < P * P) {
+      const int tx = px + tid % P - R, ty = py + tid / P - R;
+      uint32_t w = 0;
+      int known = 0;
+      if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H && __ldcg(&s.omega[(size_t)ty * s.W + tx]) == 0) {
+        w = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
+        known = 1;
+      }
+      tgt[(tid / P) * G::TP + tid % P] = w;
+      tl.known[tid] = (uint8_t)known;
     }
     __syncthreads();
-    int prev_px = -1000000, prev_py = -1000000;
-    while (!tl.stop) {
-      const int px = tl.px, py = tl.py;
-      if (leader) {
-        const unsigned long long t_a = globaltimer();
-        spec_phase<R>(s, usm);
-        __syncthreads();
-        if (tid == 0) tl.flag = wait_arrivals(tc, (unsigned)(tsize >= 2 ? ns : 0), ea.err, limit);
-        __syncthreads();
-        if (tsize >= 2) {
-          bool stop = true;
-          int npx = 0, npy = 0;
-          if (tl.flag) {
-            const unsigned long long t_b = globaltimer();
-            update_phase<R>(s, tpart, ns, usm);
-            __syncthreads();
-            stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
-            npx = __ldcg(&c->px);
-            npy = __ldcg(&c->py);
-            if (tid == 0) {
-              const unsigned long long t_c = globaltimer();
-              c->t_search += t_b - t_a;
-              c->t_update += t_c - t_b;
-              c->timed_iters += 1;
-            }
-          }
-          __syncthreads();
-          if (tid == 0) {
-            tc->arrive = 0u;
-            st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
-            tl.stop = stop;
-            tl.px = npx;
-            tl.py = npy;
-          }
-          ++epoch;
-          __syncthreads();
-          continue;
+    if (tid < P) {
+      uint32_t m = 0;
+      for (int dx = 0; dx < P; ++dx) m |= (uint32_t)tl.known[tid * P + dx] << dx;
+      rowmask[tid] = m;
+    }
+    __syncthreads();
+    unsigned long long best = ~0ull;
+    int cur = 0;
+    bool ok = true;
+    for (int b = b0; b < nbatch; b += ns) {
+      const int nb = b + ns;
+      if (tid == 0 && nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1]);
+      const int gx = b % ncg, gy = b / ncg;
+      const int qx0 = xb + 128 * gx + lane * 4, qy0 = s.cy0 + B * gy + warp * SRW;
+      int cnt[SRW][4];
+#pragma unroll
+      for (int o = 0; o < SRW; ++o)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int qx = qx0 + k, qy = qy0 + o;
+          cnt[o][k] = (qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1) ? __ldcg(&s.count[(size_t)qy * s.W + qx]) : 1;
         }
+      bool got = true;
+      if (b != b0 || need0) {
+        got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
+        if (cur) ph1 ^= 1; else ph0 ^= 1;
       }
+      uint32_t acc[SRW][4];
+      compute_rows<R, SRW>(cur ? stage1 : stage0, warp * SRW, tgt, rowmask, acc);
+#pragma unroll
+      for (int o = 0; o < SRW; ++o)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (cnt[o][k] == 0) {
+            const unsigned idx = (unsigned)((qy0 + o) * s.W + qx0 + k);
+            const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
+            best = key < best ? key : best;
+          }
+      if (__syncthreads_or(!got)) {  // a bounded wait gave up: stop uniformly
+        ok = false;
+        if (nb < nbatch) {
+          mbar_wait(&tl.full[cur ^ 1], cur ? ph0 : ph1, limit);
+          if (cur) ph0 ^= 1; else ph1 ^= 1;
+        }
+        break;
+      }
+      cur ^= 1;
+    }
+    // the tile stays resident when it is this CTA's only batch (the leader's
+    // shared memory is reused by its update phase)
+    resident = ok && !leader && b0 + ns >= nbatch && b0 < nbatch;
+    if (!ok && tid == 0) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
+    return block_min_u64(best, tl.red64);
+  };
+
+  while (!tl.stop) {
+    const int px = tl.px, py = tl.py;
+    if (leader) {
+      const unsigned long long t_a = globaltimer();
+      spec_phase<R>(s, usm);
+      __syncthreads();
       if (searcher) {
-        // first batch: reuse the resident tile unless the last fill touched it
-        const int b0 = rank;
-        const bool need0 = !resident ||
-                           (abs(prev_px - (xb + 128 * (b0 % ncg) + 64)) <= 64 + 2 * R + 4 &&
-                            abs(prev_py - (s.cy0 + B * (b0 / ncg) + B / 2)) <= B / 2 + 2 * R + 1);
-        auto issue = [&](int b, uint32_t* st, uint64_t* bar) {
-          const int gx = b % ncg, gy = b / ncg;
-          asm volatile("fence.proxy.async;" ::: "memory");
-          mbar_expect_tx(bar, (uint32_t)(G::BW * G::BH * 4));
-          tma_load_2d(st, map, xb - R + 128 * gx, s.cy0 + B * gy - R, bar);
-        };
-        if (tid == 0 && b0 < nbatch && need0) issue(b0, stage0, &tl.full[0]);
-        // target patch: one thread per pixel, then the row masks
-        if (tid < P * P) {
-          const int tx = px + tid % P - R, ty = py + tid / P - R;
-          uint32_t w = 0;
-          int known = 0;
-          if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H &&
-              __ldcg(&s.omega[(size_t)ty * s.W + tx]) == 0) {
-            w = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
-            known = 1;
-          }
-          tgt[(tid / P) * G::TP + tid % P] = w;
-          tl.known[tid] = (uint8_t)known;
-        }
+        const unsigned long long best = search_round(px, py);
+        if (tid == 0) tpart[rank] = best;
+      }
+      if (tid == 0) tl.flag = wait_arrivals(tc, n_wait, ea.err, limit);
+      __syncthreads();
+      bool stop = true;
+      int npx = 0, npy = 0;
+      if (tl.flag) {
+        const unsigned long long t_b = globaltimer();
+        update_phase<R>(s, tpart, ns, usm);
         __syncthreads();
-        if (tid < P) {
-          uint32_t m = 0;
-          for (int dx = 0; dx < P; ++dx) m |= (uint32_t)tl.known[tid * P + dx] << dx;
-          rowmask[tid] = m;
-        }
-        __syncthreads();
-        unsigned long long best = ~0ull;
-        int cur = 0;
-        bool ok = true;
-        for (int b = b0; b < nbatch; b += ns) {
-          const int nb = b + ns;
-          if (tid == 0 && nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1]);
-          const int gx = b % ncg, gy = b / ncg;
-          const int qx0 = xb + 128 * gx + lane * 4, qy0 = s.cy0 + B * gy + warp * SRW;
-          int cnt[SRW][4];
-#pragma unroll
-          for (int o = 0; o < SRW; ++o)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const int qx = qx0 + k, qy = qy0 + o;
-              cnt[o][k] = (qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1)
-                              ? __ldcg(&s.count[(size_t)qy * s.W + qx])
-                              : 1;
-            }
-          bool got = true;
-          if (b != b0 || need0) {
-            got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
-            if (cur) ph1 ^= 1; else ph0 ^= 1;
-          }
-          uint32_t acc[SRW][4];
-          compute_rows<R, SRW>(cur ? stage1 : stage0, warp * SRW, tgt, rowmask, acc);
-#pragma unroll
-          for (int o = 0; o < SRW; ++o)
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (cnt[o][k] == 0) {
-                const unsigned idx = (unsigned)((qy0 + o) * s.W + qx0 + k);
-                const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
-                best = key < best ? key : best;
-              }
-          if (__syncthreads_or(!got)) {
-            ok = false;
-            if (nb < nbatch) {
-              mbar_wait(&tl.full[cur ^ 1], cur ? ph0 : ph1, limit);
-              if (cur) ph0 ^= 1; else ph1 ^= 1;
-            }
-            break;
-          }
-          cur ^= 1;
-        }
-        // the tile stays resident when it is this CTA's only batch
-        resident = ok && tsize >= 2 && b0 + ns >= nbatch && b0 < nbatch;
-        if (!ok && tid == 0) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
-        best = block_min_u64(best, tl.red64);
-        if (tsize == 1) {
-          // team of one: apply the iteration right away
-          if (tid == 0) tpart[0] = best;
-          __threadfence();
-          __syncthreads();
-          const unsigned long long t_b = globaltimer();
-          update_phase<R>(s, tpart, 1, usm);
-          __syncthreads();
-          if (tid == 0) {
-            c->t_update += globaltimer() - t_b;
-            c->timed_iters += 1;
-            tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
-            tl.px = __ldcg(&c->px);
-            tl.py = __ldcg(&c->py);
-          }
-          resident = false;
-          prev_px = px;
-          prev_py = py;
-          __syncthreads();
-          continue;
-        }
+        stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
+        npx = __ldcg(&c->px);
+        npy = __ldcg(&c->py);
         if (tid == 0) {
-          tpart[rank] = best;
-          red_release_add(&tc->arrive, 1u);
+          c->t_search += t_b - t_a;
+          c->t_update += globaltimer() - t_b;
+          c->timed_iters += 1;
         }
       }
-      // searchers and idle CTAs: wait for the next round
+      __syncthreads();
       if (tid == 0) {
-        const unsigned long long v = wait_pub(tc, epoch, ea.err, limit);
-        tl.stop = ((v >> 62) & 1ull) != 0;
-        tl.px = (int)((v >> 32) & 0x7fff);
-        tl.py = (int)((v >> 47) & 0x7fff);
+        tc->arrive = 0u;
+        st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
+        tl.stop = stop;
+        tl.px = npx;
+        tl.py = npy;
       }
       ++epoch;
       prev_px = px;
       prev_py = py;
       __syncthreads();
       if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+      continue;
     }
+    if (searcher) {
+      const unsigned long long best = search_round(px, py);
+      if (tid == 0) {
+        tpart[rank] = best;
+        red_release_add(&tc->arrive, 1u);
+      }
+    }
+    // searchers and idle CTAs: wait for the next round
+    if (tid == 0) {
+      const unsigned long long v = wait_pub(tc, epoch, ea.err, limit);
+      tl.stop = ((v >> 62) & 1ull) != 0;
+      tl.px = (int)((v >> 32) & 0x7fff);
+      tl.py = (int)((v >> 47) & 0x7fff);
+    }
+    ++epoch;
+    prev_px = px;
+    prev_py = py;
+    __syncthreads();
+    if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
   }
   x.ph0 = ph0;
   x.ph1 = ph1;

@@ -12,13 +12,14 @@ __device__ inline unsigned long long ld_acquire64_pub(const unsigned long long* 
   return v;
 }
 
-template <int SRW>
+// Dispatch on the image's patch radius and search rows per warp.
 __device__ inline void run_by_radius(const EngineArgs& ea, int j, EngCtx& x) {
+  const bool two = ea.imgs[j].srw == 2;
   switch (ea.imgs[j].r) {
 #define INP_CASE(R)                                  \
   case R:                                            \
-    if (SRW == 1) run_image_r##R##_s1(ea, j, x);     \
-    else run_image_r##R##_s2(ea, j, x);              \
+    if (two) run_image_r##R##_s2(ea, j, x);          \
+    else run_image_r##R##_s1(ea, j, x);              \
     break;
     INP_CASE(1) INP_CASE(2) INP_CASE(3) INP_CASE(4) INP_CASE(5) INP_CASE(6) INP_CASE(7)
     INP_CASE(8)
@@ -28,7 +29,6 @@ __device__ inline void run_by_radius(const EngineArgs& ea, int j, EngCtx& x) {
   }
 }
 
-template <int SRW>
 __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EngCtx x;
@@ -51,27 +51,20 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
   x.ph1 = 0;
   x.epoch = (unsigned)ld_acquire64_pub(&x.tc->pub);
   for (int li = ea.team_img_off[team]; li < ea.team_img_off[team + 1]; ++li)
-    run_by_radius<SRW>(ea, ea.team_img[li], x);
+    run_by_radius(ea, ea.team_img[li], x);
 }
 
-template <int SRW>
-static cudaError_t set_smem(size_t smem) {
-  return cudaFuncSetAttribute(k_engine<SRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-cudaError_t engine_occupancy(int srw, size_t smem, int* blocks_per_sm) {
-  cudaError_t e = srw == 2 ? set_smem<2>(smem) : set_smem<1>(smem);
+cudaError_t engine_occupancy(size_t smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return srw == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine<2>, kEngThreads, smem)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine<1>, kEngThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine, kEngThreads, smem);
 }
 
-cudaError_t engine_launch(int srw, size_t smem, const EngineArgs& ea, int grid, cudaStream_t st) {
-  cudaError_t e = srw == 2 ? set_smem<2>(smem) : set_smem<1>(smem);
+cudaError_t engine_launch(size_t smem, const EngineArgs& ea, int grid, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<EngineArgs*>(&ea)};
-  const void* fn = srw == 2 ? (const void*)k_engine<2> : (const void*)k_engine<1>;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kEngThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel((const void*)k_engine, dim3(grid), dim3(kEngThreads), args, smem, st);
 }
 
 }  // namespace inp

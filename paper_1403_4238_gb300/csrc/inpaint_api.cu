@@ -6,6 +6,7 @@
 // device: one CUDA graph whose conditional while-node repeats
 // [findBestPatch search -> copy/update + next selection] until the update
 // kernel reports an empty Omega, so no host round trip happens per iteration.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -50,6 +51,8 @@ struct inpaint_ctx {
   uint8_t* rgb_stage = nullptr;   // 3*W*H
   uint8_t* mask_stage = nullptr;  // W*H
   double* conf_stage = nullptr;   // W*H (import only)
+  uint8_t* orig_rgb = nullptr;    // 3*W*H, batch members only: input kept for reset
+  uint8_t* orig_mask = nullptr;   // W*H
   Ctrl* h_ctrl = nullptr;         // pinned mirror of the control block
   int* h_limit = nullptr;         // pinned staging for iter_limit
   std::vector<std::pair<void*, size_t>> allocs;
@@ -180,6 +183,24 @@ bool use_engine(const inpaint_ctx* c) {
   return c->r <= 8;
 }
 
+// Rows per warp from an autotuner table: lines "radius max_pixels rows";
+// the first line with this radius and max_pixels >= W*H wins; 0 if none.
+int tuned_rows_per_warp(const char* path, int r, long long pixels) {
+  if (!path) return 0;
+  FILE* f = fopen(path, "r");
+  if (!f) return 0;
+  int rr = 0, rows = 0, out = 0;
+  long long mp = 0;
+  while (fscanf(f, "%d %lld %d", &rr, &mp, &rows) == 3) {
+    if (rr == r && pixels <= mp && (rows == 1 || rows == 2)) {
+      out = rows;
+      break;
+    }
+  }
+  fclose(f);
+  return out;
+}
+
 // Candidate rows per warp in a search batch (a batch is 16 warps x rows x
 // 128 columns): 2 when every CTA still gets about two batches, else 1.
 int pick_rows_per_warp(const ImgState& s, int grid) {
@@ -201,18 +222,20 @@ int setup_engine(inpaint_ctx* c) {
   const EngineFns* f = engine_fns(c->r);
   if (!f) return INPAINT_ERR_UNSUPPORTED;
   int bps = 0;
-  CK(engine_occupancy(sr ? sr : 2, f->smem_bytes(sr ? sr : 2), &bps));
+  CK(engine_occupancy(f->smem_bytes(2), &bps));
   if (bps < 1) {
     g_last_error = "engine kernel does not fit on an SM";
     return INPAINT_ERR_UNSUPPORTED;
   }
   const int grid = sms * bps;
+  if (!sr) sr = tuned_rows_per_warp(c->opt.tuning_file, c->r, (long long)c->W * c->H);
   if (!sr) sr = pick_rows_per_warp(c->st, grid);
   c->eng_smem = f->smem_bytes(sr);
-  CK(engine_occupancy(sr, c->eng_smem, &bps));
+  CK(engine_occupancy(c->eng_smem, &bps));
   const int g2 = sms * (bps < 1 ? 1 : bps);
   c->eng_grid = g2 < grid ? g2 : grid;
   c->eng_sr = sr;
+  c->st.srw = sr;
   if (!alloc_n(c, c->d_img, 1) || !alloc_n(c, c->d_tmap, 1) ||
       !alloc_n(c, c->d_ints, (size_t)c->eng_grid + 5) || !alloc_n(c, c->d_team, 1) ||
       !alloc_n(c, c->d_epart, (size_t)c->eng_grid) || !alloc_n(c, c->d_err, 1))
@@ -254,7 +277,7 @@ int run_engine(inpaint_ctx* c) {
   if (rc) return rc;
   CK(cudaMemsetAsync(c->d_team, 0, sizeof(TeamCtl), c->stream));
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-  CK(engine_launch(c->eng_sr, c->eng_smem, c->ea, c->eng_grid, c->stream));
+  CK(engine_launch(c->eng_smem, c->ea, c->eng_grid, c->stream));
   CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   return INPAINT_OK;
 }
@@ -620,5 +643,343 @@ const char* inpaint_status_str(int s) {
 }
 
 const char* inpaint_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+
+// ---------------------------------------------------------------- batch
+
+struct inpaint_batch {
+  int n = 0;
+  inpaint_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<inpaint_ctx*> ctx;
+  int grid = 0, n_teams = 0;
+  size_t smem = 0;
+  std::vector<int> img_team, team_size;
+  std::vector<std::pair<void*, size_t>> allocs;
+  EngineArgs ea{};
+  int* d_err = nullptr;
+  TeamCtl* d_teams = nullptr;
+  int* h_pinned = nullptr;  // [0] err, [1..n] iteration limits
+  Ctrl* h_ctrls = nullptr;  // n mirrors
+
+  void* dalloc(size_t bytes) {
+    void* p = nullptr;
+    if (opt.dev_alloc)
+      p = opt.dev_alloc(bytes, (void*)stream, opt.alloc_user);
+    else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess)
+      p = nullptr;
+    if (p) allocs.emplace_back(p, bytes);
+    return p;
+  }
+  void release() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto& a : allocs) {
+      if (opt.dev_free)
+        opt.dev_free(a.first, a.second, (void*)stream, opt.alloc_user);
+      else
+        cudaFreeAsync(a.first, stream);
+    }
+    allocs.clear();
+    for (inpaint_ctx* c : ctx) inpaint_destroy(c);
+    ctx.clear();
+    if (stream) cudaStreamSynchronize(stream);
+    if (h_pinned) cudaFreeHost(h_pinned);
+    if (h_ctrls) cudaFreeHost(h_ctrls);
+    h_pinned = nullptr;
+    h_ctrls = nullptr;
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+  }
+};
+
+namespace {
+
+template <class T>
+bool balloc(inpaint_batch* b, T*& p, size_t n) {
+  p = static_cast<T*>(b->dalloc(n * sizeof(T)));
+  return p != nullptr;
+}
+
+// Teams: with fewer images than CTAs every image gets its own team, sized in
+// proportion to its estimated work (|Omega| x valid candidates, i.e. the
+// exhaustive evaluation count up to the patch area), at least one CTA; with
+// more images than CTAs every CTA is a team and images are dealt longest
+// first to the least loaded team.
+void plan_teams(const std::vector<double>& work, int grid, std::vector<int>& team_size,
+                std::vector<int>& img_team, std::vector<std::vector<int>>& team_imgs) {
+  const int n = (int)work.size();
+  img_team.assign(n, 0);
+  if (n >= grid) {
+    team_size.assign(grid, 1);
+    team_imgs.assign(grid, {});
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<double> load(grid, 0.0);
+    for (int i : order) {
+      const int t = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[t] += work[i];
+      img_team[i] = t;
+      team_imgs[t].push_back(i);
+    }
+    return;
+  }
+  double total = 0.0;
+  for (double w : work) total += w;
+  const int extra = grid - n;
+  team_size.assign(n, 1);
+  team_imgs.assign(n, {});
+  std::vector<std::pair<double, int>> rem;
+  int used = 0;
+  for (int i = 0; i < n; ++i) {
+    const double share = total > 0 ? extra * work[i] / total : (double)extra / n;
+    const int k = (int)share;
+    team_size[i] += k;
+    used += k;
+    rem.emplace_back(share - k, i);
+  }
+  std::sort(rem.begin(), rem.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+    return a.first > b.first;
+  });
+  for (int k = 0; k < extra - used; ++k) team_size[rem[k % n].second] += 1;
+  for (int i = 0; i < n; ++i) {
+    img_team[i] = i;
+    team_imgs[i].push_back(i);
+  }
+}
+
+int batch_create_impl(const inpaint_image* images, int n, const inpaint_options* opt,
+                      inpaint_batch** out) {
+  if (!out || !images || n < 1) return INPAINT_ERR_ARG;
+  *out = nullptr;
+  inpaint_batch* b = new (std::nothrow) inpaint_batch();
+  if (!b) return INPAINT_ERR_NOMEM;
+  auto fail = [&](int code) {
+    b->release();
+    delete b;
+    return code;
+  };
+  inpaint_options_default(&b->opt);
+  if (opt) b->opt = *opt;
+  if (b->opt.form != INPAINT_FORM_PLAIN) {
+    g_last_error = "the batched form runs the plain search";
+    return fail(INPAINT_ERR_UNSUPPORTED);
+  }
+  if (b->opt.cuda_stream) {
+    b->stream = (cudaStream_t)b->opt.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(INPAINT_ERR_CUDA);
+    b->own_stream = true;
+  }
+  b->n = n;
+  inpaint_options o = b->opt;
+  o.cuda_stream = (void*)b->stream;
+  o.loop_mode = INPAINT_LOOP_ENGINE;
+  for (int i = 0; i < n; ++i) {
+    const inpaint_image& im = images[i];
+    if (im.patch_radius < 1 || im.patch_radius > 8) {
+      char buf[128];
+      snprintf(buf, sizeof buf, "batch image %d: patch radius must be 1..8", i);
+      g_last_error = buf;
+      return fail(INPAINT_ERR_ARG);
+    }
+    inpaint_ctx* c = nullptr;
+    const int rc = create_impl(im.rgb, im.width, im.height, im.rgb_stride_bytes, im.mask,
+                               im.mask_stride_bytes, im.patch_radius, &o, &c);
+    if (rc < 0) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "batch image %d: %s", i, g_last_error.c_str());
+      g_last_error = buf;
+      return fail(rc);
+    }
+    b->ctx.push_back(c);
+    const size_t px = (size_t)im.width * im.height;
+    if (!alloc_n(c, c->orig_rgb, 3 * px) || !alloc_n(c, c->orig_mask, px)) return fail(INPAINT_ERR_NOMEM);
+    if (cudaMemcpyAsync(c->orig_rgb, c->rgb_stage, 3 * px, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->orig_mask, c->mask_stage, px, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+      return fail(INPAINT_ERR_CUDA);
+  }
+  // grid and teams
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(INPAINT_ERR_CUDA);
+  size_t smem_max = 0;
+  for (inpaint_ctx* c : b->ctx) smem_max = std::max(smem_max, engine_fns(c->r)->smem_bytes(2));
+  int bps = 0;
+  if (engine_occupancy(smem_max, &bps) != cudaSuccess || bps < 1) return fail(INPAINT_ERR_UNSUPPORTED);
+  b->grid = sms * bps;
+  std::vector<double> work(n);
+  for (int i = 0; i < n; ++i)
+    work[i] = (double)std::max(1, b->ctx[i]->h_ctrl->remaining) * std::max(1, b->ctx[i]->h_ctrl->n_valid);
+  std::vector<std::vector<int>> team_imgs;
+  std::vector<int> tsz;
+  plan_teams(work, b->grid, tsz, b->img_team, team_imgs);
+  b->n_teams = (int)tsz.size();
+  b->team_size = tsz;
+  // per-image search rows, tensor maps, device copies of the states
+  std::vector<ImgState> imgs(n);
+  std::vector<CUtensorMap> maps(n);
+  b->smem = 0;
+  for (int i = 0; i < n; ++i) {
+    inpaint_ctx* c = b->ctx[i];
+    int sr = b->opt.tile_rows;
+    if (!sr) sr = tuned_rows_per_warp(b->opt.tuning_file, c->r, (long long)c->W * c->H);
+    if (!sr) sr = pick_rows_per_warp(c->st, tsz[b->img_team[i]]);
+    c->st.srw = sr;
+    imgs[i] = c->st;
+    if (make_image_tmap(c->st, sr, &maps[i]) != 0) {
+      g_last_error = "cuTensorMapEncodeTiled failed";
+      return fail(INPAINT_ERR_CUDA);
+    }
+    b->smem = std::max(b->smem, engine_fns(c->r)->smem_bytes(sr));
+  }
+  std::vector<int> ints;
+  const int G = b->grid, T = b->n_teams;
+  std::vector<int> first(T + 1, 0), off(T + 1, 0), lst;
+  for (int t = 0; t < T; ++t) {
+    first[t + 1] = first[t] + tsz[t];
+    off[t + 1] = off[t] + (int)team_imgs[t].size();
+    for (int i : team_imgs[t]) lst.push_back(i);
+  }
+  ints.resize((size_t)G);
+  for (int t = 0; t < T; ++t)
+    for (int k = first[t]; k < first[t + 1]; ++k) ints[k] = t;
+  const size_t o_first = ints.size();
+  ints.insert(ints.end(), first.begin(), first.end());
+  const size_t o_off = ints.size();
+  ints.insert(ints.end(), off.begin(), off.end());
+  const size_t o_lst = ints.size();
+  ints.insert(ints.end(), lst.begin(), lst.end());
+  ImgState* d_imgs = nullptr;
+  CUtensorMap* d_maps = nullptr;
+  int* d_ints = nullptr;
+  unsigned long long* d_part = nullptr;
+  if (!balloc(b, d_imgs, n) || !balloc(b, d_maps, n) || !balloc(b, d_ints, ints.size()) ||
+      !balloc(b, b->d_teams, T) || !balloc(b, d_part, G) || !balloc(b, b->d_err, 1))
+    return fail(INPAINT_ERR_NOMEM);
+  if (cudaMallocHost(&b->h_pinned, sizeof(int) * (n + 1)) != cudaSuccess ||
+      cudaMallocHost(&b->h_ctrls, sizeof(Ctrl) * n) != cudaSuccess)
+    return fail(INPAINT_ERR_NOMEM);
+  if (cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(ImgState) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d_maps, maps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return fail(INPAINT_ERR_CUDA);
+  EngineArgs& ea = b->ea;
+  ea.imgs = d_imgs;
+  ea.tmaps = d_maps;
+  ea.cta_team = d_ints;
+  ea.team_first = d_ints + o_first;
+  ea.team_img_off = d_ints + o_off;
+  ea.team_img = d_ints + o_lst;
+  ea.teams = b->d_teams;
+  ea.partials = d_part;
+  ea.err = b->d_err;
+  ea.wait_limit_ns = 4000000000ull;
+  *out = b;
+  return INPAINT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int inpaint_batch_create(const inpaint_image* images, int n, const inpaint_options* opt,
+                         inpaint_batch** out) {
+  try {
+    return batch_create_impl(images, n, opt, out);
+  } catch (...) {
+    return INPAINT_ERR_NOMEM;
+  }
+}
+
+int inpaint_batch_reset(inpaint_batch* b) {
+  if (!b) return INPAINT_ERR_ARG;
+  for (inpaint_ctx* c : b->ctx)
+    CK(launch_init(c->st, c->orig_rgb, 3 * c->W, c->orig_mask, c->W, c->sat, nullptr, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  return INPAINT_OK;
+}
+
+int inpaint_batch_run(inpaint_batch* b, int max_iters, int* status_out) {
+  if (!b) return INPAINT_ERR_ARG;
+  const int n = b->n;
+  for (int i = 0; i < n; ++i)
+    CK(cudaMemcpyAsync(b->h_ctrls + i, b->ctx[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < n; ++i) {
+    const Ctrl& h = b->h_ctrls[i];
+    long long lim = (long long)h.iter + std::max(h.remaining, 0);
+    if (max_iters > 0 && (long long)h.iter + max_iters < lim) lim = (long long)h.iter + max_iters;
+    b->h_pinned[1 + i] = (int)std::min<long long>(lim, INT_MAX);
+    CK(cudaMemcpyAsync(&b->ctx[i]->st.ctrl->iter_limit, &b->h_pinned[1 + i], sizeof(int),
+                       cudaMemcpyHostToDevice, b->stream));
+  }
+  CK(cudaMemsetAsync(b->d_teams, 0, sizeof(TeamCtl) * b->n_teams, b->stream));
+  CK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+  CK(engine_launch(b->smem, b->ea, b->grid, b->stream));
+  CK(cudaMemcpyAsync(b->h_pinned, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  for (int i = 0; i < n; ++i)
+    CK(cudaMemcpyAsync(b->h_ctrls + i, b->ctx[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < n; ++i) {
+    // restore the unlimited iteration bound for later calls
+    b->h_pinned[1 + i] = INT_MAX;
+    CK(cudaMemcpyAsync(&b->ctx[i]->st.ctrl->iter_limit, &b->h_pinned[1 + i], sizeof(int),
+                       cudaMemcpyHostToDevice, b->stream));
+  }
+  CK(cudaStreamSynchronize(b->stream));
+  if (status_out)
+    for (int i = 0; i < n; ++i) {
+      const Ctrl& h = b->h_ctrls[i];
+      status_out[i] = h.status != 0 ? h.status : (h.iter == 0 && h.remaining == 0 ? INPAINT_DONE : INPAINT_OK);
+    }
+  if (b->h_pinned[0]) {
+    g_last_error = "a bounded device wait in the persistent engine gave up";
+    return INPAINT_ERR_TIMEOUT;
+  }
+  return INPAINT_OK;
+}
+
+int inpaint_batch_result(const inpaint_batch* b, int i, uint8_t* rgb_out, int stride_bytes,
+                         int* iterations, uint64_t* evals) {
+  if (!b || i < 0 || i >= b->n) return INPAINT_ERR_ARG;
+  const inpaint_ctx* c = b->ctx[i];
+  if (rgb_out) {
+    const int rc = inpaint_result(c, rgb_out, stride_bytes, nullptr);
+    if (rc) return rc;
+  }
+  if (iterations || evals) {
+    const int rc = read_ctrl(c);
+    if (rc) return rc;
+    if (iterations) *iterations = c->h_ctrl->iter;
+    if (evals) *evals = c->h_ctrl->evals;
+  }
+  return INPAINT_OK;
+}
+
+int inpaint_batch_plan(const inpaint_batch* b, int* grid, int* n_teams, int* team_of_image,
+                       int* team_size_of_image, int* rows_per_warp) {
+  if (!b) return INPAINT_ERR_ARG;
+  if (grid) *grid = b->grid;
+  if (n_teams) *n_teams = b->n_teams;
+  for (int i = 0; i < b->n; ++i) {
+    if (team_of_image) team_of_image[i] = b->img_team[i];
+    if (team_size_of_image) team_size_of_image[i] = b->team_size[b->img_team[i]];
+    if (rows_per_warp) rows_per_warp[i] = b->ctx[i]->st.srw;
+  }
+  return INPAINT_OK;
+}
+
+void inpaint_batch_destroy(inpaint_batch* b) {
+  if (!b) return;
+  b->release();
+  delete b;
+}
 
 }  // extern "C"

@@ -72,10 +72,10 @@ const EngineFns* engine_fns_r7();
 const EngineFns* engine_fns_r8();
 
 const EngineFns* engine_fns(int r);
-// Engine kernel (engine_multi.cu) for SRW rows per warp; smem = the largest
-// engine_fns(r)->smem_bytes(srw) over the radii of the images in the launch.
-cudaError_t engine_occupancy(int srw, size_t smem, int* blocks_per_sm);
-cudaError_t engine_launch(int srw, size_t smem, const EngineArgs& ea, int grid, cudaStream_t st);
+// The engine kernel (engine_multi.cu); smem = the largest
+// engine_fns(r)->smem_bytes(srw) over the images of the launch.
+cudaError_t engine_occupancy(size_t smem, int* blocks_per_sm);
+cudaError_t engine_launch(size_t smem, const EngineArgs& ea, int grid, cudaStream_t st);
 int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out);
 cudaError_t launch_update_fast(const ImgState& s, unsigned long long cond, int use_cond,
                                cudaStream_t st);

@@ -79,9 +79,18 @@ constexpr int kSpecNotFront = -1;  // in the image, not on the post-fill front
 struct SpecBuf {
   double C[kSpecMax];
   int nrm[kSpecMax];
+  uint16_t front[kSpecMax];  // window indices of the post-fill front pixels
+  int nfront;
   int iter;    // iteration described
   int filled;  // pixels that iteration fills
 };
+
+// Thread that handles entry k of a compact work list: consecutive entries go
+// to warps 0..3 in turn (one warp per SM sub-partition), so a short list of
+// long FP64 dependency chains uses all four sub-partitions with few active
+// lanes each.
+__device__ inline int list_thread(int k) { return ((k & 3) << 5) | ((k >> 2) & 31) | ((k >> 7) << 7); }
+__device__ inline int list_entry(int t) { return ((t & 31) << 2) | ((t >> 5) & 3) | ((t >> 7) << 7); }
 
 // Data-term table: D = (dot / sqrt(nn)) / 510 for every |n|^2 = nn a Sobel
 // normal of a binary mask can take (nx, ny in [-4, 4]) and dot in [0, 2040].
@@ -113,6 +122,7 @@ struct ImgState {
   int cx0, cx1, cy0, cy1;  // candidate-centre rectangle (inclusive)
   int t0x, t0y, t1x, t1y;  // level-0 / level-1 tile grid sizes
   int trace_cap;
+  int srw;                 // engine search rows per warp (1 or 2)
   int n_partial;           // search CTAs writing partial[]
   uint32_t* img;
   uint8_t* omega;

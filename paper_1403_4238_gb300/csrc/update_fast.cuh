@@ -47,6 +47,8 @@ struct __align__(16) UpdSmem {
   uint8_t om[G::NS * G::NS];  // 0 known, 1 Omega, 2 outside the image
   uint8_t gr[G::NS * G::NS];
   uint8_t filled[G::P * G::P];
+  uint16_t list[G::NW * G::NW];
+  int nlist;
   unsigned long long red64[32];
   int red32[32];
 };
@@ -237,23 +239,33 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm) {
   }
   const int filled = block_sum_int(my, sm.red32);  // includes __syncthreads
   SpecBuf* sp = s.spec;
+  // post-fill front of the window, compacted
+  if (threadIdx.x == 0) sm.nlist = 0;
+  __syncthreads();
   for (int i = threadIdx.x; i < NW * NW; i += blockDim.x) {
-    const int wx = i % NW - R2, wy = i / NW - R2;
-    const int lx = RB + wx, ly = RB + wy, l = ly * NS + lx;
+    const int l = (RB + i / NW - R2) * NS + RB + i % NW - R2;
     int nrm = kSpecOutside;
-    double cc = 0.0;
     if (sm.om[l] != 2) {
       nrm = kSpecNotFront;
-      if (front_local(sm.om, l, NS)) {
-        const int x = px + wx, y = py + wy;
-        cc = conf_local<R>(sm, s, lx, ly, x, y);
-        nrm = normal_local<R>(sm, s, lx, ly, x, y);
-      }
+      if (front_local(sm.om, l, NS)) sm.list[atomicAdd(&sm.nlist, 1)] = (uint16_t)i;
     }
-    sp->C[i] = cc;
-    sp->nrm[i] = nrm;
+    sp->nrm[i] = nrm;  // front entries are overwritten below
+  }
+  __syncthreads();
+  const int nfront = sm.nlist;
+  // one long FP64 chain per front pixel, spread over the four sub-partitions
+  for (int t = threadIdx.x; t < ((nfront + 127) & ~127); t += blockDim.x) {
+    const int k = list_entry(t);
+    if (k >= nfront) continue;
+    const int i = sm.list[k];
+    const int wx = i % NW - R2, wy = i / NW - R2;
+    const int lx = RB + wx, ly = RB + wy, x = px + wx, y = py + wy;
+    sp->C[i] = conf_local<R>(sm, s, lx, ly, x, y);
+    sp->nrm[i] = normal_local<R>(sm, s, lx, ly, x, y);
+    sp->front[k] = (uint16_t)i;
   }
   if (threadIdx.x == 0) {
+    sp->nfront = nfront;
     sp->iter = it;
     sp->filled = filled;
   }
@@ -286,8 +298,10 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   for (int i = tid; i < NW * NW; i += nt) {
     sm.sC[i] = __ldcg(&sp->C[i]);
     sm.snrm[i] = __ldcg(&sp->nrm[i]);
+    sm.list[i] = __ldcg(&sp->front[i]);
   }
   const int spec_iter = __ldcg(&sp->iter), spec_filled = __ldcg(&sp->filled);
+  const int nfront = __ldcg(&sp->nfront);
   best = block_min_u64(best, sm.red64);
   if (best == ~0ull) {
     if (tid == 0) c->status = INPAINT_ERR_NO_SOURCE;
@@ -350,27 +364,32 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   }
   __syncthreads();
 
-  // priorities of the window and validity counts around p^
+  // priorities of the window (front pixels from the compact list, spread
+  // over the sub-partitions; the others get key 0) and validity counts
   int newly = 0;
-  for (int i = tid; i < NW * NW + NC * NC; i += nt) {
-    if (i < NW * NW) {
-      const int nrm = sm.snrm[i];
-      if (nrm == kSpecOutside) continue;
+  const int nlist = (nfront + 127) & ~127;
+  for (int t = tid; t < nlist + NW * NW + NC * NC; t += nt) {
+    if (t < nlist) {
+      const int k = list_entry(t);
+      if (k >= nfront) continue;
+      const int i = sm.list[k];
       const int wx = i % NW - R2, wy = i / NW - R2;
+      int gx, gy;
+      isophote_local<R>(sm, RB + wx, RB + wy, &gx, &gy);
+      const double cc = sm.sC[i];
+      const int nrm = sm.snrm[i];
+      const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
       const size_t p = (size_t)(py + wy) * W + px + wx;
-      unsigned long long key = 0ull;
-      double cc = 0.0;
-      if (nrm != kSpecNotFront) {
-        int gx, gy;
-        isophote_local<R>(sm, RB + wx, RB + wy, &gx, &gy);
-        cc = sm.sC[i];
-        const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
-        key = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
-      }
-      s.prio[p] = key;
+      s.prio[p] = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
       s.pconf[p] = cc;
+    } else if (t < nlist + NW * NW) {
+      const int i = t - nlist;
+      if (sm.snrm[i] != kSpecNotFront) continue;  // outside, or a front pixel
+      const size_t p = (size_t)(py + i / NW - R2) * W + px + i % NW - R2;
+      s.prio[p] = 0ull;
+      s.pconf[p] = 0.0;
     } else {
-      const int j = i - NW * NW;
+      const int j = t - nlist - NW * NW;
       const int wy = j / NC - 2 * R, wx = j % NC - 2 * R;
       const int x = px + wx, y = py + wy;
       if (x < 0 || x >= W || y < 0 || y >= H) continue;

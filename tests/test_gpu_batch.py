@@ -1,0 +1,93 @@
+"""Batched form: one persistent launch over many images of mixed sizes and
+radii gives, for every image, exactly the single-image result (which the
+parity tests tie to the oracle), and the oracle's result on small images."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1403_4238_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_4238_gb300 import api as _api
+    return _api
+
+
+def mixed_cases(n, seed, wmax=200, hmax=150):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        W = int(rng.integers(40, wmax))
+        H = int(rng.integers(36, hmax))
+        r = int(rng.integers(1, 9))
+        r = min(r, (min(W, H) - 1) // 4)
+        c = synth.tiny(W, H, int(rng.integers(0, 2**31)), r=max(r, 1))
+        out.append((c.rgb, c.mask, c.r))
+    return out
+
+
+def test_batch_equals_oracle_mixed_radii(api):
+    cases = mixed_cases(12, 7)
+    with api.Batch(cases) as b:
+        st = b.run()
+        for i, (rgb, mask, r) in enumerate(cases):
+            ref = oracle.run(rgb, mask, r)
+            out, iters, evals = b.result(i)
+            assert st[i] == 0 and iters == ref.iters
+            assert evals == ref.evals
+            assert np.array_equal(out, ref.rgb), i
+
+
+def test_batch_equals_solo_runs_and_reset(api):
+    cases = [(c.rgb, c.mask, c.r) for c in synth.batch_cases(6, seed=11)]
+    solo = []
+    for rgb, mask, r in cases:
+        with api.Inpainter(rgb, mask, r) as ip:
+            ip.run()
+            solo.append(ip.result())
+    with api.Batch(cases) as b:
+        plan = b.plan()
+        assert sum(set(zip(plan["team"], plan["team_size"])) and plan["team_size"]) >= 1
+        for rep in range(2):  # second pass after a device-side reset
+            if rep:
+                b.reset()
+            st = b.run()
+            assert all(v == 0 for v in st)
+            for i in range(len(cases)):
+                out, _, _ = b.result(i)
+                assert np.array_equal(out, solo[i]), (rep, i)
+
+
+def test_batch_more_images_than_ctas(api):
+    # more images than CTAs: every CTA is a team working through a list
+    cases = []
+    for i in range(170):
+        c = synth.tiny(20 + i % 7, 18 + i % 5, 1000 + i, r=1 + i % 2)
+        cases.append((c.rgb, c.mask, c.r))
+    with api.Batch(cases) as b:
+        plan = b.plan()
+        assert plan["teams"] == plan["grid"] and plan["grid"] < len(cases)
+        st = b.run()
+        assert all(v == 0 for v in st)
+        for i in range(0, len(cases), 17):
+            rgb, mask, r = cases[i]
+            assert np.array_equal(b.result(i)[0], oracle.run(rgb, mask, r).rgb), i
+
+
+def test_batch_iteration_limit_and_resume(api):
+    cases = mixed_cases(5, 3)
+    refs = [oracle.run(rgb, m, r) for rgb, m, r in cases]
+    with api.Batch(cases) as b:
+        b.run(max_iters=3)
+        for i in range(len(cases)):
+            assert b.result(i)[1] == min(3, refs[i].iters)
+        b.run()
+        for i in range(len(cases)):
+            out, iters, _ = b.result(i)
+            assert iters == refs[i].iters and np.array_equal(out, refs[i].rgb)
