@@ -266,6 +266,63 @@ int inpaint_batch_plan(const inpaint_batch* b, int* grid, int* n_teams, int* tea
 /* Releases everything (after synchronising the batch's stream). */
 void inpaint_batch_destroy(inpaint_batch* b);
 
+/* ---- Serving loop: continuous batching of object-removal requests ----
+ * A server owns a worker thread and a CUDA stream.  Submitted requests wait
+ * in a FIFO queue; between scheduler ticks the worker admits queued requests
+ * while slots are free and the estimated device memory of the admitted ones
+ * stays within the budget (their state stays on the device until they
+ * finish); each tick is one persistent engine launch over every active slot
+ * (up to iters_per_tick iterations each), after which finished requests
+ * release their memory and their result waits for inpaint_server_poll.
+ * A request's result does not depend on what else is in flight: it equals
+ * inpaint_run on that image alone. */
+#define INPAINT_PENDING 2   /* inpaint_server_poll: request not finished yet */
+
+typedef struct inpaint_server inpaint_server;
+
+typedef struct {
+  double t_submit, t_admit, t_done;  /* seconds on the server's clock */
+  int status;                        /* inpaint_status of the removal */
+  int iterations;
+  uint64_t evals;
+  int width, height;
+} inpaint_request_info;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, failed, ticks;
+  int queued, active;
+  size_t hbm_used, hbm_budget;
+  double busy_s;                     /* worker time spent admitting and in ticks */
+} inpaint_server_stats;
+
+/* hbm_budget_bytes: limit on the estimated device memory of active requests;
+ * max_slots: limit on simultaneously active requests; iters_per_tick: engine
+ * iterations per slot per tick (<= 0: 64).  opt as for inpaint_create
+ * (cuda_stream ignored: the server makes its own). */
+int inpaint_server_create(size_t hbm_budget_bytes, int max_slots, int iters_per_tick,
+                          const inpaint_options* opt, inpaint_server** out);
+
+/* Queues a request (inputs are copied; radius 1..8).  *id identifies it. */
+int inpaint_server_submit(inpaint_server* s, const inpaint_image* img, uint64_t* id);
+
+/* INPAINT_PENDING while request id runs; once done, copies its result (RGB,
+ * rows of stride_bytes, nullable) and info (nullable), forgets the request
+ * and returns INPAINT_OK (INPAINT_ERR_ARG for an unknown id). */
+int inpaint_server_poll(inpaint_server* s, uint64_t id, uint8_t* rgb_out, int stride_bytes,
+                        inpaint_request_info* info);
+
+/* Blocks until nothing is queued or active, or timeout_s passed
+ * (INPAINT_ERR_TIMEOUT). */
+int inpaint_server_wait_idle(inpaint_server* s, double timeout_s);
+
+int inpaint_server_stats_get(inpaint_server* s, inpaint_server_stats* st);
+
+/* Seconds on the server's clock (the clock of inpaint_request_info). */
+double inpaint_server_clock(const inpaint_server* s);
+
+/* Stops the worker (after the current tick) and releases everything. */
+void inpaint_server_destroy(inpaint_server* s);
+
 /* Releases the context and all its device memory (after synchronising its
  * stream).  NULL is a no-op. */
 void inpaint_destroy(inpaint_ctx* ctx);

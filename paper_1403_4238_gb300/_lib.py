@@ -97,6 +97,19 @@ class Peaks(ctypes.Structure):
                 ("sm_clock_mhz", ctypes.c_double), ("sm_count", ctypes.c_int)]
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("evals", ctypes.c_uint64),
+                ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("ticks", ctypes.c_uint64),
+                ("queued", ctypes.c_int), ("active", ctypes.c_int), ("hbm_used", ctypes.c_size_t),
+                ("hbm_budget", ctypes.c_size_t), ("busy_s", ctypes.c_double)]
+
+
 STEP_DTYPE = np.dtype(
     [("iter", np.int32), ("px", np.int32), ("py", np.int32), ("qx", np.int32), ("qy", np.int32),
      ("ssd", np.uint32), ("priority", np.float64), ("confidence", np.float64),
@@ -154,6 +167,13 @@ SIGNATURES = {
     "inpaint_batch_result": (_I, [_P, _I, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_uint64)]),
     "inpaint_batch_plan": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _P, _P]),
     "inpaint_batch_destroy": (None, [_P]),
+    "inpaint_server_create": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "inpaint_server_submit": (_I, [_P, ctypes.POINTER(Image), ctypes.POINTER(ctypes.c_uint64)]),
+    "inpaint_server_poll": (_I, [_P, ctypes.c_uint64, _P, _I, ctypes.POINTER(RequestInfo)]),
+    "inpaint_server_wait_idle": (_I, [_P, ctypes.c_double]),
+    "inpaint_server_stats_get": (_I, [_P, ctypes.POINTER(ServerStats)]),
+    "inpaint_server_clock": (ctypes.c_double, [_P]),
+    "inpaint_server_destroy": (None, [_P]),
     "inpaint_loop_timing": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(_I)]),
 }
@@ -185,6 +205,6 @@ class InpaintError(RuntimeError):
 
 
 STATUS = {
-    "OK": 0, "DONE": 1, "ERR_ARG": -1, "ERR_NOMEM": -2, "ERR_CUDA": -3, "ERR_NO_SOURCE": -4,
+    "OK": 0, "DONE": 1, "PENDING": 2, "ERR_ARG": -1, "ERR_NOMEM": -2, "ERR_CUDA": -3, "ERR_NO_SOURCE": -4,
     "ERR_TIMEOUT": -5, "ERR_UNSUPPORTED": -6, "ERR_INTERNAL": -7,
 }

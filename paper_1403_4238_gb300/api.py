@@ -294,3 +294,80 @@ class Batch:
         _check(self.lib.inpaint_batch_plan(self.b, ctypes.byref(g), ctypes.byref(t), team, size, rows),
                "inpaint_batch_plan")
         return dict(grid=g.value, teams=t.value, team=list(team), team_size=list(size), rows=list(rows))
+
+
+class Server:
+    """Continuous-batching object-removal server (inpaint_server_*).
+
+    A worker thread inside the library admits queued requests into device
+    slots (HBM budget, slot limit) between scheduler ticks; each tick is one
+    persistent launch over all active slots.  submit() returns an id at once;
+    poll(id) returns None while pending, else (rgb, info dict).
+    """
+
+    def __init__(self, hbm_budget_bytes: int = 40 << 30, max_slots: int = 256, iters_per_tick: int = 64,
+                 *, tile_rows: int = 0, tuning_file: str | None = None):
+        torch = _torch()
+        self.lib = _lib.load()
+        torch.cuda.current_device()
+        opt = Options()
+        self.lib.inpaint_options_default(ctypes.byref(opt))
+        opt.tile_rows = int(tile_rows)
+        self._tf = tuning_file.encode() if tuning_file else None
+        opt.tuning_file = self._tf
+        self._opt = opt
+        s = ctypes.c_void_p()
+        _check(self.lib.inpaint_server_create(int(hbm_budget_bytes), int(max_slots), int(iters_per_tick),
+                                              ctypes.byref(opt), ctypes.byref(s)), "inpaint_server_create")
+        self.s = s
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.inpaint_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, rgb, mask, r: int) -> int:
+        rgb = np.ascontiguousarray(rgb, np.uint8)
+        mask = np.ascontiguousarray(mask, np.uint8)
+        H, W = mask.shape
+        im = _lib.Image(rgb.ctypes.data, W, H, 3 * W, mask.ctypes.data, W, int(r))
+        rid = ctypes.c_uint64()
+        _check(self.lib.inpaint_server_submit(self.s, ctypes.byref(im), ctypes.byref(rid)),
+               "inpaint_server_submit")
+        self.shapes[rid.value] = (H, W)
+        return rid.value
+
+    def poll(self, rid: int):
+        H, W = self.shapes[rid]
+        out = np.zeros((H, W, 3), np.uint8)
+        info = _lib.RequestInfo()
+        rc = _check(self.lib.inpaint_server_poll(self.s, ctypes.c_uint64(rid), out.ctypes.data, 3 * W,
+                                                 ctypes.byref(info)), "inpaint_server_poll")
+        if rc == _lib.STATUS["PENDING"]:
+            return None
+        del self.shapes[rid]
+        return out, {f: getattr(info, f) for f, _ in _lib.RequestInfo._fields_}
+
+    def wait_idle(self, timeout_s: float = 600.0):
+        return _check(self.lib.inpaint_server_wait_idle(self.s, float(timeout_s)), "inpaint_server_wait_idle")
+
+    def stats(self):
+        st = _lib.ServerStats()
+        _check(self.lib.inpaint_server_stats_get(self.s, ctypes.byref(st)), "inpaint_server_stats_get")
+        return {f: getattr(st, f) for f, _ in _lib.ServerStats._fields_}
+
+    def clock(self) -> float:
+        return float(self.lib.inpaint_server_clock(self.s))

@@ -7,7 +7,12 @@
 // [findBestPatch search -> copy/update + next selection] until the update
 // kernel reports an empty Omega, so no host round trip happens per iteration.
 #include <algorithm>
+#include <chrono>
 #include <climits>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -647,25 +652,15 @@ const char* inpaint_last_error(void) { return g_last_error.c_str(); }
 }  // extern "C"
 
 
-// ---------------------------------------------------------------- batch
+// ---------------------------------------------------------------- engine sets
 
-struct inpaint_batch {
-  int n = 0;
+// Device memory owned by a batch or a server (inpaint_options allocator hooks
+// when given, else cudaMallocAsync on its stream).
+struct DevAlloc {
   inpaint_options opt{};
   cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  std::vector<inpaint_ctx*> ctx;
-  int grid = 0, n_teams = 0;
-  size_t smem = 0;
-  std::vector<int> img_team, team_size;
   std::vector<std::pair<void*, size_t>> allocs;
-  EngineArgs ea{};
-  int* d_err = nullptr;
-  TeamCtl* d_teams = nullptr;
-  int* h_pinned = nullptr;  // [0] err, [1..n] iteration limits
-  Ctrl* h_ctrls = nullptr;  // n mirrors
-
-  void* dalloc(size_t bytes) {
+  void* alloc(size_t bytes) {
     void* p = nullptr;
     if (opt.dev_alloc)
       p = opt.dev_alloc(bytes, (void*)stream, opt.alloc_user);
@@ -674,34 +669,38 @@ struct inpaint_batch {
     if (p) allocs.emplace_back(p, bytes);
     return p;
   }
+  void free(void* p) {
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i].first == p) {
+        if (opt.dev_free)
+          opt.dev_free(p, allocs[i].second, (void*)stream, opt.alloc_user);
+        else
+          cudaFreeAsync(p, stream);
+        allocs.erase(allocs.begin() + (long)i);
+        return;
+      }
+  }
   void release() {
-    if (stream) cudaStreamSynchronize(stream);
-    for (auto& a : allocs) {
-      if (opt.dev_free)
-        opt.dev_free(a.first, a.second, (void*)stream, opt.alloc_user);
-      else
-        cudaFreeAsync(a.first, stream);
-    }
-    allocs.clear();
-    for (inpaint_ctx* c : ctx) inpaint_destroy(c);
-    ctx.clear();
-    if (stream) cudaStreamSynchronize(stream);
-    if (h_pinned) cudaFreeHost(h_pinned);
-    if (h_ctrls) cudaFreeHost(h_ctrls);
-    h_pinned = nullptr;
-    h_ctrls = nullptr;
-    if (own_stream && stream) cudaStreamDestroy(stream);
-    stream = nullptr;
+    while (!allocs.empty()) free(allocs.back().first);
   }
 };
 
-namespace {
+// One persistent launch over a set of contexts: team plan, per-image search
+// rows and TMA descriptors, and the device arrays the engine reads.
+struct EngineSet {
+  int grid = 0, n_teams = 0;
+  size_t smem = 0;
+  std::vector<int> img_team, team_size;
+  EngineArgs ea{};
+  void* d_block = nullptr;
+  size_t d_cap = 0;
+  int* d_err = nullptr;
+  int* h_pinned = nullptr;  // [0] err, [1..] iteration limits
+  Ctrl* h_ctrls = nullptr;
+  int h_cap = 0;
+};
 
-template <class T>
-bool balloc(inpaint_batch* b, T*& p, size_t n) {
-  p = static_cast<T*>(b->dalloc(n * sizeof(T)));
-  return p != nullptr;
-}
+namespace {
 
 // Teams: with fewer images than CTAs every image gets its own team, sized in
 // proportion to its estimated work (|Omega| x valid candidates, i.e. the
@@ -751,8 +750,220 @@ void plan_teams(const std::vector<double>& work, int grid, std::vector<int>& tea
   }
 }
 
-int batch_create_impl(const inpaint_image* images, int n, const inpaint_options* opt,
-                      inpaint_batch** out) {
+int grid_for(const std::vector<inpaint_ctx*>& cs, int* grid) {
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  size_t smem_max = 0;
+  for (inpaint_ctx* c : cs) smem_max = std::max(smem_max, engine_fns(c->r)->smem_bytes(2));
+  int bps = 0;
+  CK(engine_occupancy(smem_max, &bps));
+  if (bps < 1) return INPAINT_ERR_UNSUPPORTED;
+  *grid = sms * bps;
+  return INPAINT_OK;
+}
+
+// Plans the teams for the contexts (work estimates from their last control
+// block mirrors) and uploads everything the engine reads.
+int engine_set_prepare(EngineSet& es, const std::vector<inpaint_ctx*>& cs, const std::vector<double>& work,
+                       const inpaint_options& opt, DevAlloc& da, cudaStream_t st) {
+  const int n = (int)cs.size();
+  int rc = grid_for(cs, &es.grid);
+  if (rc) return rc;
+  std::vector<std::vector<int>> team_imgs;
+  plan_teams(work, es.grid, es.team_size, es.img_team, team_imgs);
+  es.n_teams = (int)es.team_size.size();
+  const int G = es.grid, T = es.n_teams;
+  std::vector<ImgState> imgs(n);
+  std::vector<CUtensorMap> maps(n);
+  es.smem = 0;
+  for (int i = 0; i < n; ++i) {
+    inpaint_ctx* c = cs[i];
+    int sr = opt.tile_rows;
+    if (!sr) sr = tuned_rows_per_warp(opt.tuning_file, c->r, (long long)c->W * c->H);
+    if (!sr) sr = pick_rows_per_warp(c->st, es.team_size[es.img_team[i]]);
+    c->st.srw = sr;
+    imgs[i] = c->st;
+    if (make_image_tmap(c->st, sr, &maps[i]) != 0) {
+      g_last_error = "cuTensorMapEncodeTiled failed";
+      return INPAINT_ERR_CUDA;
+    }
+    es.smem = std::max(es.smem, engine_fns(c->r)->smem_bytes(sr));
+  }
+  std::vector<int> first(T + 1, 0), off(T + 1, 0), ints((size_t)G);
+  std::vector<int> lst;
+  for (int t = 0; t < T; ++t) {
+    first[t + 1] = first[t] + es.team_size[t];
+    off[t + 1] = off[t] + (int)team_imgs[t].size();
+    for (int i : team_imgs[t]) lst.push_back(i);
+    for (int k = first[t]; k < first[t + 1]; ++k) ints[k] = t;
+  }
+  const size_t o_first = ints.size();
+  ints.insert(ints.end(), first.begin(), first.end());
+  const size_t o_off = ints.size();
+  ints.insert(ints.end(), off.begin(), off.end());
+  const size_t o_lst = ints.size();
+  ints.insert(ints.end(), lst.begin(), lst.end());
+  // one device block: states | maps | teams | partials | ints | err
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_imgs = up(sizeof(ImgState) * n), b_maps = up(sizeof(CUtensorMap) * n);
+  const size_t b_teams = up(sizeof(TeamCtl) * T), b_part = up(sizeof(unsigned long long) * G);
+  const size_t b_ints = up(sizeof(int) * ints.size()), b_err = 256;
+  const size_t need = b_imgs + b_maps + b_teams + b_part + b_ints + b_err;
+  if (need > es.d_cap) {
+    if (es.d_block) da.free(es.d_block);
+    es.d_block = da.alloc(need * 2);
+    if (!es.d_block) return INPAINT_ERR_NOMEM;
+    es.d_cap = need * 2;
+  }
+  if (n + 1 > es.h_cap) {
+    if (es.h_pinned) cudaFreeHost(es.h_pinned);
+    if (es.h_ctrls) cudaFreeHost(es.h_ctrls);
+    es.h_pinned = nullptr;
+    es.h_ctrls = nullptr;
+    const int cap = 2 * (n + 1);
+    if (cudaMallocHost(&es.h_pinned, sizeof(int) * cap) != cudaSuccess ||
+        cudaMallocHost(&es.h_ctrls, sizeof(Ctrl) * cap) != cudaSuccess)
+      return INPAINT_ERR_NOMEM;
+    es.h_cap = cap;
+  }
+  uint8_t* base = (uint8_t*)es.d_block;
+  ImgState* d_imgs = (ImgState*)base;
+  CUtensorMap* d_maps = (CUtensorMap*)(base + b_imgs);
+  TeamCtl* d_teams = (TeamCtl*)(base + b_imgs + b_maps);
+  unsigned long long* d_part = (unsigned long long*)(base + b_imgs + b_maps + b_teams);
+  int* d_ints = (int*)(base + b_imgs + b_maps + b_teams + b_part);
+  es.d_err = (int*)(base + b_imgs + b_maps + b_teams + b_part + b_ints);
+  CK(cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(ImgState) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_maps, maps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  EngineArgs& ea = es.ea;
+  ea.imgs = d_imgs;
+  ea.tmaps = d_maps;
+  ea.cta_team = d_ints;
+  ea.team_first = d_ints + o_first;
+  ea.team_img_off = d_ints + o_off;
+  ea.team_img = d_ints + o_lst;
+  ea.teams = d_teams;
+  ea.partials = d_part;
+  ea.err = es.d_err;
+  ea.wait_limit_ns = 4000000000ull;
+  return INPAINT_OK;
+}
+
+// One launch: every context runs until its Omega is empty, it fails, or it
+// has done max_iters more iterations (<= 0: no limit).  Control blocks are
+// read back into es.h_ctrls.  Returns INPAINT_ERR_TIMEOUT if a bounded
+// device wait gave up.
+int engine_set_run(EngineSet& es, const std::vector<inpaint_ctx*>& cs, int max_iters, cudaStream_t st) {
+  const int n = (int)cs.size();
+  for (int i = 0; i < n; ++i)
+    CK(cudaMemcpyAsync(es.h_ctrls + i, cs[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i) {
+    const Ctrl& h = es.h_ctrls[i];
+    long long lim = (long long)h.iter + std::max(h.remaining, 0);
+    if (max_iters > 0 && (long long)h.iter + max_iters < lim) lim = (long long)h.iter + max_iters;
+    es.h_pinned[1 + i] = (int)std::min<long long>(lim, INT_MAX);
+    CK(cudaMemcpyAsync(&cs[i]->st.ctrl->iter_limit, &es.h_pinned[1 + i], sizeof(int),
+                       cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemsetAsync((void*)es.ea.teams, 0, sizeof(TeamCtl) * es.n_teams, st));
+  CK(cudaMemsetAsync(es.d_err, 0, sizeof(int), st));
+  CK(engine_launch(es.smem, es.ea, es.grid, st));
+  CK(cudaMemcpyAsync(es.h_pinned, es.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  for (int i = 0; i < n; ++i)
+    CK(cudaMemcpyAsync(es.h_ctrls + i, cs[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i) {  // back to the unlimited bound for later calls
+    es.h_pinned[1 + i] = INT_MAX;
+    CK(cudaMemcpyAsync(&cs[i]->st.ctrl->iter_limit, &es.h_pinned[1 + i], sizeof(int),
+                       cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  if (es.h_pinned[0]) {
+    g_last_error = "a bounded device wait in the persistent engine gave up";
+    return INPAINT_ERR_TIMEOUT;
+  }
+  return INPAINT_OK;
+}
+
+void engine_set_free(EngineSet& es) {
+  if (es.h_pinned) cudaFreeHost(es.h_pinned);
+  if (es.h_ctrls) cudaFreeHost(es.h_ctrls);
+  es.h_pinned = nullptr;
+  es.h_ctrls = nullptr;
+}
+
+// Creates a context for one image on the given stream, with a device copy of
+// its input kept for resets.
+int make_member(const inpaint_image& im, const inpaint_options& base, cudaStream_t st, int index,
+                inpaint_ctx** out) {
+  *out = nullptr;
+  if (im.patch_radius < 1 || im.patch_radius > 8) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "image %d: patch radius must be 1..8", index);
+    g_last_error = buf;
+    return INPAINT_ERR_ARG;
+  }
+  inpaint_options o = base;
+  o.cuda_stream = (void*)st;
+  o.loop_mode = INPAINT_LOOP_ENGINE;
+  inpaint_ctx* c = nullptr;
+  int rc = create_impl(im.rgb, im.width, im.height, im.rgb_stride_bytes, im.mask, im.mask_stride_bytes,
+                       im.patch_radius, &o, &c);
+  if (rc < 0) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "image %d: %s", index, g_last_error.c_str());
+    g_last_error = buf;
+    return rc;
+  }
+  const size_t px = (size_t)im.width * im.height;
+  if (!alloc_n(c, c->orig_rgb, 3 * px) || !alloc_n(c, c->orig_mask, px)) {
+    inpaint_destroy(c);
+    return INPAINT_ERR_NOMEM;
+  }
+  if (cudaMemcpyAsync(c->orig_rgb, c->rgb_stage, 3 * px, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->orig_mask, c->mask_stage, px, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+    inpaint_destroy(c);
+    return INPAINT_ERR_CUDA;
+  }
+  *out = c;
+  return INPAINT_OK;
+}
+
+double work_of(const Ctrl& h) {
+  return (double)std::max(1, h.remaining) * std::max(1, h.n_valid);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- batch
+
+struct inpaint_batch {
+  int n = 0;
+  inpaint_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<inpaint_ctx*> ctx;
+  DevAlloc da;
+  EngineSet es;
+  void release() {
+    if (stream) cudaStreamSynchronize(stream);
+    da.release();
+    engine_set_free(es);
+    for (inpaint_ctx* c : ctx) inpaint_destroy(c);
+    ctx.clear();
+    if (stream) cudaStreamSynchronize(stream);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+  }
+};
+
+namespace {
+
+int batch_create_impl(const inpaint_image* images, int n, const inpaint_options* opt, inpaint_batch** out) {
   if (!out || !images || n < 1) return INPAINT_ERR_ARG;
   *out = nullptr;
   inpaint_batch* b = new (std::nothrow) inpaint_batch();
@@ -771,116 +982,22 @@ int batch_create_impl(const inpaint_image* images, int n, const inpaint_options*
   if (b->opt.cuda_stream) {
     b->stream = (cudaStream_t)b->opt.cuda_stream;
   } else {
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
-      return fail(INPAINT_ERR_CUDA);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(INPAINT_ERR_CUDA);
     b->own_stream = true;
   }
+  b->da.opt = b->opt;
+  b->da.stream = b->stream;
   b->n = n;
-  inpaint_options o = b->opt;
-  o.cuda_stream = (void*)b->stream;
-  o.loop_mode = INPAINT_LOOP_ENGINE;
-  for (int i = 0; i < n; ++i) {
-    const inpaint_image& im = images[i];
-    if (im.patch_radius < 1 || im.patch_radius > 8) {
-      char buf[128];
-      snprintf(buf, sizeof buf, "batch image %d: patch radius must be 1..8", i);
-      g_last_error = buf;
-      return fail(INPAINT_ERR_ARG);
-    }
-    inpaint_ctx* c = nullptr;
-    const int rc = create_impl(im.rgb, im.width, im.height, im.rgb_stride_bytes, im.mask,
-                               im.mask_stride_bytes, im.patch_radius, &o, &c);
-    if (rc < 0) {
-      char buf[160];
-      snprintf(buf, sizeof buf, "batch image %d: %s", i, g_last_error.c_str());
-      g_last_error = buf;
-      return fail(rc);
-    }
-    b->ctx.push_back(c);
-    const size_t px = (size_t)im.width * im.height;
-    if (!alloc_n(c, c->orig_rgb, 3 * px) || !alloc_n(c, c->orig_mask, px)) return fail(INPAINT_ERR_NOMEM);
-    if (cudaMemcpyAsync(c->orig_rgb, c->rgb_stage, 3 * px, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(c->orig_mask, c->mask_stage, px, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
-      return fail(INPAINT_ERR_CUDA);
-  }
-  // grid and teams
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return fail(INPAINT_ERR_CUDA);
-  size_t smem_max = 0;
-  for (inpaint_ctx* c : b->ctx) smem_max = std::max(smem_max, engine_fns(c->r)->smem_bytes(2));
-  int bps = 0;
-  if (engine_occupancy(smem_max, &bps) != cudaSuccess || bps < 1) return fail(INPAINT_ERR_UNSUPPORTED);
-  b->grid = sms * bps;
   std::vector<double> work(n);
-  for (int i = 0; i < n; ++i)
-    work[i] = (double)std::max(1, b->ctx[i]->h_ctrl->remaining) * std::max(1, b->ctx[i]->h_ctrl->n_valid);
-  std::vector<std::vector<int>> team_imgs;
-  std::vector<int> tsz;
-  plan_teams(work, b->grid, tsz, b->img_team, team_imgs);
-  b->n_teams = (int)tsz.size();
-  b->team_size = tsz;
-  // per-image search rows, tensor maps, device copies of the states
-  std::vector<ImgState> imgs(n);
-  std::vector<CUtensorMap> maps(n);
-  b->smem = 0;
   for (int i = 0; i < n; ++i) {
-    inpaint_ctx* c = b->ctx[i];
-    int sr = b->opt.tile_rows;
-    if (!sr) sr = tuned_rows_per_warp(b->opt.tuning_file, c->r, (long long)c->W * c->H);
-    if (!sr) sr = pick_rows_per_warp(c->st, tsz[b->img_team[i]]);
-    c->st.srw = sr;
-    imgs[i] = c->st;
-    if (make_image_tmap(c->st, sr, &maps[i]) != 0) {
-      g_last_error = "cuTensorMapEncodeTiled failed";
-      return fail(INPAINT_ERR_CUDA);
-    }
-    b->smem = std::max(b->smem, engine_fns(c->r)->smem_bytes(sr));
+    inpaint_ctx* c = nullptr;
+    const int rc = make_member(images[i], b->opt, b->stream, i, &c);
+    if (rc < 0) return fail(rc);
+    b->ctx.push_back(c);
+    work[i] = work_of(*c->h_ctrl);
   }
-  std::vector<int> ints;
-  const int G = b->grid, T = b->n_teams;
-  std::vector<int> first(T + 1, 0), off(T + 1, 0), lst;
-  for (int t = 0; t < T; ++t) {
-    first[t + 1] = first[t] + tsz[t];
-    off[t + 1] = off[t] + (int)team_imgs[t].size();
-    for (int i : team_imgs[t]) lst.push_back(i);
-  }
-  ints.resize((size_t)G);
-  for (int t = 0; t < T; ++t)
-    for (int k = first[t]; k < first[t + 1]; ++k) ints[k] = t;
-  const size_t o_first = ints.size();
-  ints.insert(ints.end(), first.begin(), first.end());
-  const size_t o_off = ints.size();
-  ints.insert(ints.end(), off.begin(), off.end());
-  const size_t o_lst = ints.size();
-  ints.insert(ints.end(), lst.begin(), lst.end());
-  ImgState* d_imgs = nullptr;
-  CUtensorMap* d_maps = nullptr;
-  int* d_ints = nullptr;
-  unsigned long long* d_part = nullptr;
-  if (!balloc(b, d_imgs, n) || !balloc(b, d_maps, n) || !balloc(b, d_ints, ints.size()) ||
-      !balloc(b, b->d_teams, T) || !balloc(b, d_part, G) || !balloc(b, b->d_err, 1))
-    return fail(INPAINT_ERR_NOMEM);
-  if (cudaMallocHost(&b->h_pinned, sizeof(int) * (n + 1)) != cudaSuccess ||
-      cudaMallocHost(&b->h_ctrls, sizeof(Ctrl) * n) != cudaSuccess)
-    return fail(INPAINT_ERR_NOMEM);
-  if (cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(ImgState) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-      cudaMemcpyAsync(d_maps, maps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-      cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-      cudaStreamSynchronize(b->stream) != cudaSuccess)
-    return fail(INPAINT_ERR_CUDA);
-  EngineArgs& ea = b->ea;
-  ea.imgs = d_imgs;
-  ea.tmaps = d_maps;
-  ea.cta_team = d_ints;
-  ea.team_first = d_ints + o_first;
-  ea.team_img_off = d_ints + o_off;
-  ea.team_img = d_ints + o_lst;
-  ea.teams = b->d_teams;
-  ea.partials = d_part;
-  ea.err = b->d_err;
-  ea.wait_limit_ns = 4000000000ull;
+  const int rc = engine_set_prepare(b->es, b->ctx, work, b->opt, b->da, b->stream);
+  if (rc < 0) return fail(rc);
   *out = b;
   return INPAINT_OK;
 }
@@ -908,42 +1025,13 @@ int inpaint_batch_reset(inpaint_batch* b) {
 
 int inpaint_batch_run(inpaint_batch* b, int max_iters, int* status_out) {
   if (!b) return INPAINT_ERR_ARG;
-  const int n = b->n;
-  for (int i = 0; i < n; ++i)
-    CK(cudaMemcpyAsync(b->h_ctrls + i, b->ctx[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
-  CK(cudaStreamSynchronize(b->stream));
-  for (int i = 0; i < n; ++i) {
-    const Ctrl& h = b->h_ctrls[i];
-    long long lim = (long long)h.iter + std::max(h.remaining, 0);
-    if (max_iters > 0 && (long long)h.iter + max_iters < lim) lim = (long long)h.iter + max_iters;
-    b->h_pinned[1 + i] = (int)std::min<long long>(lim, INT_MAX);
-    CK(cudaMemcpyAsync(&b->ctx[i]->st.ctrl->iter_limit, &b->h_pinned[1 + i], sizeof(int),
-                       cudaMemcpyHostToDevice, b->stream));
-  }
-  CK(cudaMemsetAsync(b->d_teams, 0, sizeof(TeamCtl) * b->n_teams, b->stream));
-  CK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
-  CK(engine_launch(b->smem, b->ea, b->grid, b->stream));
-  CK(cudaMemcpyAsync(b->h_pinned, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
-  for (int i = 0; i < n; ++i)
-    CK(cudaMemcpyAsync(b->h_ctrls + i, b->ctx[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
-  CK(cudaStreamSynchronize(b->stream));
-  for (int i = 0; i < n; ++i) {
-    // restore the unlimited iteration bound for later calls
-    b->h_pinned[1 + i] = INT_MAX;
-    CK(cudaMemcpyAsync(&b->ctx[i]->st.ctrl->iter_limit, &b->h_pinned[1 + i], sizeof(int),
-                       cudaMemcpyHostToDevice, b->stream));
-  }
-  CK(cudaStreamSynchronize(b->stream));
+  const int rc = engine_set_run(b->es, b->ctx, max_iters, b->stream);
   if (status_out)
-    for (int i = 0; i < n; ++i) {
-      const Ctrl& h = b->h_ctrls[i];
+    for (int i = 0; i < b->n; ++i) {
+      const Ctrl& h = b->es.h_ctrls[i];
       status_out[i] = h.status != 0 ? h.status : (h.iter == 0 && h.remaining == 0 ? INPAINT_DONE : INPAINT_OK);
     }
-  if (b->h_pinned[0]) {
-    g_last_error = "a bounded device wait in the persistent engine gave up";
-    return INPAINT_ERR_TIMEOUT;
-  }
-  return INPAINT_OK;
+  return rc;
 }
 
 int inpaint_batch_result(const inpaint_batch* b, int i, uint8_t* rgb_out, int stride_bytes,
@@ -966,11 +1054,11 @@ int inpaint_batch_result(const inpaint_batch* b, int i, uint8_t* rgb_out, int st
 int inpaint_batch_plan(const inpaint_batch* b, int* grid, int* n_teams, int* team_of_image,
                        int* team_size_of_image, int* rows_per_warp) {
   if (!b) return INPAINT_ERR_ARG;
-  if (grid) *grid = b->grid;
-  if (n_teams) *n_teams = b->n_teams;
+  if (grid) *grid = b->es.grid;
+  if (n_teams) *n_teams = b->es.n_teams;
   for (int i = 0; i < b->n; ++i) {
-    if (team_of_image) team_of_image[i] = b->img_team[i];
-    if (team_size_of_image) team_size_of_image[i] = b->team_size[b->img_team[i]];
+    if (team_of_image) team_of_image[i] = b->es.img_team[i];
+    if (team_size_of_image) team_size_of_image[i] = b->es.team_size[b->es.img_team[i]];
     if (rows_per_warp) rows_per_warp[i] = b->ctx[i]->st.srw;
   }
   return INPAINT_OK;
@@ -980,6 +1068,299 @@ void inpaint_batch_destroy(inpaint_batch* b) {
   if (!b) return;
   b->release();
   delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- server
+
+namespace {
+
+struct SrvReq {
+  uint64_t id = 0;
+  int W = 0, H = 0, r = 0;
+  std::vector<uint8_t> rgb, mask, out;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int status = 0, iters = 0, state = 0;  // state: 0 queued, 1 active, 2 done
+  uint64_t evals = 0;
+  size_t bytes = 0;
+  inpaint_ctx* ctx = nullptr;
+};
+
+// Upper estimate of a request's device memory (the buffers create_impl and
+// the batch member copy allocate, about 48 bytes per pixel plus the trace).
+size_t est_bytes(int W, int H, int n_omega) {
+  return (size_t)W * H * 48 + (size_t)(n_omega + 1) * sizeof(inpaint_step_info) + (1u << 20);
+}
+
+}  // namespace
+
+struct inpaint_server {
+  size_t budget = 0, used = 0;
+  int max_slots = 0, iters_per_tick = 64, device = 0;
+  inpaint_options opt{};
+  cudaStream_t stream = nullptr;
+  DevAlloc da;
+  EngineSet es;
+  std::mutex mu;
+  std::condition_variable cv, cv_idle;
+  std::deque<SrvReq*> queue;
+  std::vector<SrvReq*> active;
+  std::unordered_map<uint64_t, SrvReq*> reqs;
+  uint64_t next_id = 1;
+  int admitting = 0;  // popped from the queue, not yet active or retired
+  bool stop = false;
+  std::thread worker;
+  std::chrono::steady_clock::time_point t0;
+  inpaint_server_stats st{};
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+
+  void retire(SrvReq* q, int status) {
+    if (q->ctx) {
+      if (status >= 0) {
+        q->out.resize((size_t)q->W * q->H * 3);
+        if (inpaint_result(q->ctx, q->out.data(), 3 * q->W, nullptr) != INPAINT_OK) status = INPAINT_ERR_CUDA;
+      }
+      inpaint_destroy(q->ctx);
+      q->ctx = nullptr;
+    }
+    q->status = status;
+    q->t_done = now();
+  }
+
+  void loop() {
+    cudaSetDevice(device);
+    while (true) {
+      std::vector<SrvReq*> admit;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || !queue.empty() || !active.empty(); });
+        if (stop) return;
+        while (!queue.empty() && (int)(active.size() + admit.size()) < max_slots) {
+          SrvReq* q = queue.front();
+          int n_omega = 0;
+          for (uint8_t m : q->mask) n_omega += m != 0;
+          const size_t b = est_bytes(q->W, q->H, n_omega);
+          if (used + b > budget && !(active.empty() && admit.empty())) break;
+          queue.pop_front();
+          q->bytes = b;
+          used += b;
+          admit.push_back(q);
+        }
+        admitting = (int)admit.size();
+      }
+      const auto tb = std::chrono::steady_clock::now();
+      std::vector<SrvReq*> failed;
+      for (SrvReq* q : admit) {
+        inpaint_image im{q->rgb.data(), q->W, q->H, 3 * q->W, q->mask.data(), q->W, q->r};
+        inpaint_ctx* c = nullptr;
+        const int rc = make_member(im, opt, stream, (int)q->id, &c);
+        q->t_admit = now();
+        if (rc < 0) {
+          retire(q, rc);
+          failed.push_back(q);
+        } else {
+          q->ctx = c;
+          q->rgb.clear();
+          q->rgb.shrink_to_fit();
+          q->mask.clear();
+          q->mask.shrink_to_fit();
+        }
+      }
+      std::vector<SrvReq*> act;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        admitting = 0;
+        for (SrvReq* q : admit)
+          if (q->ctx) {
+            q->state = 1;
+            active.push_back(q);
+            st.admitted++;
+          }
+        for (SrvReq* q : failed) {
+          q->state = 2;
+          used -= q->bytes;
+          st.failed++;
+        }
+        act = active;
+      }
+      std::vector<SrvReq*> done;
+      if (!act.empty()) {
+        std::vector<inpaint_ctx*> cs;
+        std::vector<double> work;
+        for (SrvReq* q : act) {
+          cs.push_back(q->ctx);
+          work.push_back(work_of(*q->ctx->h_ctrl));
+        }
+        int rc = engine_set_prepare(es, cs, work, opt, da, stream);
+        if (rc >= 0) rc = engine_set_run(es, cs, iters_per_tick, stream);
+        for (size_t i = 0; i < act.size(); ++i) {
+          const Ctrl& h = rc >= 0 ? es.h_ctrls[i] : *act[i]->ctx->h_ctrl;
+          *act[i]->ctx->h_ctrl = h;  // mirror for the next work estimate
+          if (rc < 0 || h.status != 0 || h.remaining == 0) {
+            act[i]->iters = h.iter;
+            act[i]->evals = h.evals;
+            retire(act[i], rc < 0 ? rc : (h.status != 0 ? h.status : INPAINT_OK));
+            done.push_back(act[i]);
+          }
+        }
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      st.ticks++;
+      st.busy_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - tb).count();
+      for (SrvReq* q : done) {
+        q->state = 2;
+        used -= q->bytes;
+        if (q->status < 0) st.failed++; else st.completed++;
+        active.erase(std::find(active.begin(), active.end(), q));
+      }
+      if (idle()) cv_idle.notify_all();
+    }
+  }
+
+  bool idle() const { return queue.empty() && active.empty() && admitting == 0; }
+};
+
+extern "C" {
+
+int inpaint_server_create(size_t hbm_budget_bytes, int max_slots, int iters_per_tick,
+                          const inpaint_options* opt, inpaint_server** out) {
+  if (!out || hbm_budget_bytes == 0 || max_slots < 1) return INPAINT_ERR_ARG;
+  *out = nullptr;
+  inpaint_server* s = new (std::nothrow) inpaint_server();
+  if (!s) return INPAINT_ERR_NOMEM;
+  inpaint_options_default(&s->opt);
+  if (opt) s->opt = *opt;
+  s->opt.form = INPAINT_FORM_PLAIN;
+  s->budget = hbm_budget_bytes;
+  s->max_slots = max_slots;
+  s->iters_per_tick = iters_per_tick > 0 ? iters_per_tick : 64;
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete s;
+    return INPAINT_ERR_CUDA;
+  }
+  s->opt.cuda_stream = (void*)s->stream;
+  s->da.opt = s->opt;
+  s->da.stream = s->stream;
+  s->t0 = std::chrono::steady_clock::now();
+  s->st.hbm_budget = hbm_budget_bytes;
+  try {
+    s->worker = std::thread([s] { s->loop(); });
+  } catch (...) {
+    cudaStreamDestroy(s->stream);
+    delete s;
+    return INPAINT_ERR_NOMEM;
+  }
+  *out = s;
+  return INPAINT_OK;
+}
+
+int inpaint_server_submit(inpaint_server* s, const inpaint_image* img, uint64_t* id) {
+  if (!s || !img || !img->rgb || !img->mask || img->patch_radius < 1 || img->patch_radius > 8 ||
+      img->rgb_stride_bytes < 3 * img->width || img->mask_stride_bytes < img->width)
+    return INPAINT_ERR_ARG;
+  if (check_geometry(img->width, img->height, img->patch_radius)) return INPAINT_ERR_ARG;
+  SrvReq* q = new (std::nothrow) SrvReq();
+  if (!q) return INPAINT_ERR_NOMEM;
+  q->W = img->width;
+  q->H = img->height;
+  q->r = img->patch_radius;
+  q->rgb.resize((size_t)q->W * q->H * 3);
+  q->mask.resize((size_t)q->W * q->H);
+  for (int y = 0; y < q->H; ++y) {
+    memcpy(&q->rgb[(size_t)y * 3 * q->W], img->rgb + (size_t)y * img->rgb_stride_bytes, 3 * (size_t)q->W);
+    memcpy(&q->mask[(size_t)y * q->W], img->mask + (size_t)y * img->mask_stride_bytes, (size_t)q->W);
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    q->id = s->next_id++;
+    q->t_submit = s->now();
+    s->reqs[q->id] = q;
+    s->queue.push_back(q);
+    s->st.submitted++;
+  }
+  s->cv.notify_one();
+  if (id) *id = q->id;
+  return INPAINT_OK;
+}
+
+int inpaint_server_poll(inpaint_server* s, uint64_t id, uint8_t* rgb_out, int stride_bytes,
+                        inpaint_request_info* info) {
+  if (!s) return INPAINT_ERR_ARG;
+  SrvReq* q = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return INPAINT_ERR_ARG;
+    if (it->second->state != 2) return INPAINT_PENDING;
+    q = it->second;
+    s->reqs.erase(it);
+  }
+  if (rgb_out && !q->out.empty())
+    for (int y = 0; y < q->H; ++y)
+      memcpy(rgb_out + (size_t)y * stride_bytes, &q->out[(size_t)y * 3 * q->W], 3 * (size_t)q->W);
+  if (info) {
+    info->t_submit = q->t_submit;
+    info->t_admit = q->t_admit;
+    info->t_done = q->t_done;
+    info->status = q->status;
+    info->iterations = q->iters;
+    info->evals = q->evals;
+    info->width = q->W;
+    info->height = q->H;
+  }
+  delete q;
+  return INPAINT_OK;
+}
+
+int inpaint_server_wait_idle(inpaint_server* s, double timeout_s) {
+  if (!s) return INPAINT_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const bool ok = s->cv_idle.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                      [&] { return s->idle(); });
+  return ok ? INPAINT_OK : INPAINT_ERR_TIMEOUT;
+}
+
+int inpaint_server_stats_get(inpaint_server* s, inpaint_server_stats* out) {
+  if (!s || !out) return INPAINT_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  out->queued = (int)s->queue.size();
+  out->active = (int)s->active.size();
+  out->hbm_used = s->used;
+  out->hbm_budget = s->budget;
+  return INPAINT_OK;
+}
+
+double inpaint_server_clock(const inpaint_server* s) { return s ? s->now() : 0.0; }
+
+void inpaint_server_destroy(inpaint_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->device);
+  for (SrvReq* q : s->active) {
+    if (q->ctx) inpaint_destroy(q->ctx);
+    q->ctx = nullptr;
+  }
+  for (auto& kv : s->reqs) {
+    if (kv.second->ctx) inpaint_destroy(kv.second->ctx);
+    delete kv.second;
+  }
+  cudaStreamSynchronize(s->stream);
+  s->da.release();
+  engine_set_free(s->es);
+  cudaStreamSynchronize(s->stream);
+  cudaStreamDestroy(s->stream);
+  delete s;
 }
 
 }  // extern "C"

@@ -1,0 +1,89 @@
+"""Serving loop: requests admitted into device slots while others run give,
+each, exactly the result of running that image alone; admission respects
+the slot limit and the HBM budget; late arrivals join running ticks."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1403_4238_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_4238_gb300 import api as _api
+    return _api
+
+
+def requests(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        W = int(rng.integers(64, 320))
+        H = int(rng.integers(48, 240))
+        r = int(rng.integers(2, 6))
+        c = synth.Case("req", synth.image(W, H, 6, 30.0, 100 + i),
+                       synth.ellipse_mask(W, H, 2, 0.03, 0.08, 200 + i), r)
+        out.append((c.rgb, c.mask, c.r))
+    return out
+
+
+def alone(api, rgb, mask, r):
+    with api.Inpainter(rgb, mask, r) as ip:
+        ip.run()
+        return ip.result()
+
+
+def test_results_equal_alone_in_the_mix(api):
+    reqs = requests(10, 1)
+    with api.Server(hbm_budget_bytes=1 << 30, max_slots=6, iters_per_tick=8) as srv:
+        ids = [srv.submit(*q) for q in reqs[:6]]
+        time.sleep(0.02)
+        ids += [srv.submit(*q) for q in reqs[6:]]  # arrive while the first ones run
+        srv.wait_idle(300)
+        st = srv.stats()
+        assert st["completed"] == 10 and st["failed"] == 0 and st["ticks"] >= 2
+        for rid, q in zip(ids, reqs):
+            out, info = srv.poll(rid)
+            assert info["status"] == 0
+            assert info["t_submit"] <= info["t_admit"] <= info["t_done"]
+            assert np.array_equal(out, alone(api, *q))
+
+
+def test_budget_limits_admission(api):
+    reqs = []
+    for i in range(6):  # equal sizes: the budget fits exactly two at a time
+        c = synth.Case("req", synth.image(200, 150, 6, 30.0, 300 + i),
+                       synth.ellipse_mask(200, 150, 2, 0.05, 0.06, 400 + i), 3)
+        reqs.append((c.rgb, c.mask, c.r))
+    per = 200 * 150 * 48 + (1 << 21)
+    with api.Server(hbm_budget_bytes=2 * per, max_slots=64, iters_per_tick=4) as srv:
+        ids = [srv.submit(*q) for q in reqs]
+        peak = 0
+        t0 = time.time()
+        while srv.stats()["completed"] < len(reqs) and time.time() - t0 < 300:
+            st = srv.stats()
+            peak = max(peak, st["active"])
+            assert st["hbm_used"] <= st["hbm_budget"]
+            time.sleep(0.001)
+        assert peak <= 2
+        for rid, q in zip(ids, reqs):
+            out, info = srv.poll(rid)
+            assert np.array_equal(out, alone(api, *q))
+
+
+def test_poll_pending_and_unknown(api):
+    reqs = requests(1, 3)
+    with api.Server(hbm_budget_bytes=1 << 30, max_slots=2, iters_per_tick=1) as srv:
+        rid = srv.submit(*reqs[0])
+        first = srv.poll(rid)  # usually still pending after one tick of one iteration
+        srv.wait_idle(120)
+        if first is None:
+            out, info = srv.poll(rid)
+            assert info["status"] == 0
+        assert srv.lib.inpaint_server_poll(srv.s, 987654, None, 0, None) == -1  # unknown id
