@@ -64,6 +64,7 @@ struct inpaint_ctx {
   cudaGraph_t run_graph = nullptr;
   cudaGraphExec_t run_exec = nullptr;
   unsigned long long cond = 0;
+  TcPlan tc{};  // tensor-core search plan (form INPAINT_FORM_TC)
   // persistent engine (one team of every CTA)
   bool eng_ready = false;
   int eng_grid = 0, eng_sr = 0;
@@ -174,7 +175,10 @@ int check_geometry(int W, int H, int r) {
 }
 
 int launch_iteration(inpaint_ctx* c, int use_cond) {
-  CK(launch_search_plain(c->st, c->stream));
+  if (c->opt.form == INPAINT_FORM_TC)
+    CK(launch_search_tc(c->st, c->tc, c->stream));
+  else
+    CK(launch_search_plain(c->st, c->stream));
   if (c->r <= 8)
     CK(launch_update_fast(c->st, c->cond, use_cond, c->stream));
   else
@@ -184,7 +188,7 @@ int launch_iteration(inpaint_ctx* c, int use_cond) {
 }
 
 bool use_engine(const inpaint_ctx* c) {
-  if (c->opt.loop_mode == INPAINT_LOOP_GRAPH) return false;
+  if (c->opt.loop_mode == INPAINT_LOOP_GRAPH || c->opt.form == INPAINT_FORM_TC) return false;
   return c->r <= 8;
 }
 
@@ -348,8 +352,8 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
     g_last_error = "dev_alloc and dev_free must be given together";
     return INPAINT_ERR_ARG;
   }
-  if (o.form == INPAINT_FORM_TC) {
-    g_last_error = "tensor-core form not built yet";
+  if (o.form == INPAINT_FORM_TC && (r > 8 || o.loop_mode == INPAINT_LOOP_ENGINE)) {
+    g_last_error = "the tensor-core form supports patch_radius <= 8 in the graph loop";
     return INPAINT_ERR_UNSUPPORTED;
   }
 
@@ -390,6 +394,13 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
   s.trace_cap = (int)n_omega + 1;
   const dim3 g = search_plain_grid(s);
   s.n_partial = (int)(g.x * g.y);
+  if (o.form == INPAINT_FORM_TC) {
+    if (prepare_search_tc(s, &c->tc) != cudaSuccess) {
+      g_last_error = "tensor-core search set-up failed";
+      return fail(INPAINT_ERR_CUDA);
+    }
+    s.n_partial = c->tc.grid;
+  }
   const size_t n = (size_t)W * H;
   if (!alloc_n(c, s.img, (size_t)s.pitch * H) || !alloc_n(c, s.omega, n) || !alloc_n(c, s.gray, n) ||
       !alloc_n(c, s.conf, n) || !alloc_n(c, s.count, n) || !alloc_n(c, s.prio, n) ||
@@ -949,8 +960,25 @@ struct inpaint_batch {
   std::vector<inpaint_ctx*> ctx;
   DevAlloc da;
   EngineSet es;
+  // CUDA graphs: every member's initialisation (on kBatchAux parallel
+  // branches) and the run to completion (one persistent launch + read-back)
+  static constexpr int kBatchAux = 4;
+  cudaGraphExec_t reset_exec = nullptr, run_exec = nullptr;
+  cudaStream_t aux[kBatchAux] = {};
+  cudaEvent_t fork = nullptr, join[kBatchAux] = {};
   void release() {
     if (stream) cudaStreamSynchronize(stream);
+    if (reset_exec) cudaGraphExecDestroy(reset_exec);
+    if (run_exec) cudaGraphExecDestroy(run_exec);
+    reset_exec = run_exec = nullptr;
+    for (int k = 0; k < kBatchAux; ++k) {
+      if (aux[k]) cudaStreamDestroy(aux[k]);
+      if (join[k]) cudaEventDestroy(join[k]);
+      aux[k] = nullptr;
+      join[k] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
     da.release();
     engine_set_free(es);
     for (inpaint_ctx* c : ctx) inpaint_destroy(c);
@@ -962,6 +990,63 @@ struct inpaint_batch {
 };
 
 namespace {
+
+// Captures one stream's work into an executable graph; false (and no graph)
+// if anything in the capture fails, so callers keep the direct path.
+template <typename F>
+bool capture_graph(cudaStream_t st, cudaGraphExec_t* exec, F&& body) {
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const bool ok = body();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  bool done = ok && e == cudaSuccess && g && cudaGraphInstantiate(exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!done) {
+    *exec = nullptr;
+    cudaGetLastError();
+  }
+  return done;
+}
+
+void build_batch_graphs(inpaint_batch* b) {
+  for (int k = 0; k < inpaint_batch::kBatchAux; ++k)
+    if (cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) != cudaSuccess)
+      return;
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return;
+  capture_graph(b->stream, &b->reset_exec, [&] {
+    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return false;
+    for (int k = 0; k < inpaint_batch::kBatchAux; ++k)
+      if (cudaStreamWaitEvent(b->aux[k], b->fork, 0) != cudaSuccess) return false;
+    for (int i = 0; i < b->n; ++i) {
+      inpaint_ctx* c = b->ctx[i];
+      if (launch_init(c->st, c->orig_rgb, 3 * c->W, c->orig_mask, c->W, c->sat, nullptr,
+                      b->aux[i % inpaint_batch::kBatchAux]) != cudaSuccess)
+        return false;
+    }
+    for (int k = 0; k < inpaint_batch::kBatchAux; ++k)
+      if (cudaEventRecord(b->join[k], b->aux[k]) != cudaSuccess ||
+          cudaStreamWaitEvent(b->stream, b->join[k], 0) != cudaSuccess)
+        return false;
+    return true;
+  });
+  EngineSet& es = b->es;
+  capture_graph(b->stream, &b->run_exec, [&] {
+    if (cudaMemsetAsync((void*)es.ea.teams, 0, sizeof(TeamCtl) * es.n_teams, b->stream) != cudaSuccess ||
+        cudaMemsetAsync(es.d_err, 0, sizeof(int), b->stream) != cudaSuccess ||
+        engine_launch(es.smem, es.ea, es.grid, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(es.h_pinned, es.d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return false;
+    for (int i = 0; i < b->n; ++i)
+      if (cudaMemcpyAsync(es.h_ctrls + i, b->ctx[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                          b->stream) != cudaSuccess)
+        return false;
+    return true;
+  });
+}
 
 int batch_create_impl(const inpaint_image* images, int n, const inpaint_options* opt, inpaint_batch** out) {
   if (!out || !images || n < 1) return INPAINT_ERR_ARG;
@@ -998,6 +1083,8 @@ int batch_create_impl(const inpaint_image* images, int n, const inpaint_options*
   }
   const int rc = engine_set_prepare(b->es, b->ctx, work, b->opt, b->da, b->stream);
   if (rc < 0) return fail(rc);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(INPAINT_ERR_CUDA);
+  build_batch_graphs(b);
   *out = b;
   return INPAINT_OK;
 }
@@ -1017,6 +1104,11 @@ int inpaint_batch_create(const inpaint_image* images, int n, const inpaint_optio
 
 int inpaint_batch_reset(inpaint_batch* b) {
   if (!b) return INPAINT_ERR_ARG;
+  if (b->reset_exec) {
+    CK(cudaGraphLaunch(b->reset_exec, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return INPAINT_OK;
+  }
   for (inpaint_ctx* c : b->ctx)
     CK(launch_init(c->st, c->orig_rgb, 3 * c->W, c->orig_mask, c->W, c->sat, nullptr, b->stream));
   CK(cudaStreamSynchronize(b->stream));
@@ -1025,7 +1117,19 @@ int inpaint_batch_reset(inpaint_batch* b) {
 
 int inpaint_batch_run(inpaint_batch* b, int max_iters, int* status_out) {
   if (!b) return INPAINT_ERR_ARG;
-  const int rc = engine_set_run(b->es, b->ctx, max_iters, b->stream);
+  int rc = INPAINT_OK;
+  if (max_iters <= 0 && b->run_exec) {
+    // run to completion: the iteration bound of every member is unlimited
+    // between calls, so the captured launch needs no per-call set-up
+    CK(cudaGraphLaunch(b->run_exec, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (b->es.h_pinned[0]) {
+      g_last_error = "a bounded device wait in the persistent engine gave up";
+      rc = INPAINT_ERR_TIMEOUT;
+    }
+  } else {
+    rc = engine_set_run(b->es, b->ctx, max_iters, b->stream);
+  }
   if (status_out)
     for (int i = 0; i < b->n; ++i) {
       const Ctrl& h = b->es.h_ctrls[i];

@@ -363,6 +363,13 @@ cudaError_t launch_prio_init_fast(const ImgState& s, cudaStream_t st);  // r <= 
 const double* data_term_table(int device);  // per-device table, built on first use
 cudaError_t launch_search_plain(const ImgState& s, cudaStream_t st);
 dim3 search_plain_grid(const ImgState& s);
+// Tensor-core search (search_tc.cu), patch radius 1..8: a persistent grid over
+// tiles of 8 candidate rows; one partial key per CTA (grid partials).
+struct TcPlan {
+  int grid = 0, nx = 0, ntiles = 0, smem = 0;
+};
+cudaError_t prepare_search_tc(const ImgState& s, TcPlan* plan);
+cudaError_t launch_search_tc(const ImgState& s, const TcPlan& plan, cudaStream_t st);
 cudaError_t launch_update(const ImgState& s, int do_fill, unsigned long long cond_handle,
                           int use_cond, cudaStream_t st);
 cudaError_t launch_verify_count(const ImgState& s, cudaStream_t st);
