@@ -63,13 +63,14 @@ class Inpainter:
     radius (patch side 2r+1).  form: "plain" or "tc".  alpha: search factor
     of Eq. 6 (negative = exhaustive).  loop: "auto", "engine" (persistent
     kernel) or "graph" (conditional CUDA graph).  tile_rows: engine search
-    unit height (0 = library choice).  Inputs may be numpy arrays (host) or
+    unit height (0 = library choice); tuning_file: autotuner table
+    (paper_1403_4238_gb300.autotune) consulted when tile_rows is 0.  Inputs may be numpy arrays (host) or
     CUDA torch tensors (device, uint8, contiguous).
     """
 
     def __init__(self, rgb, mask, r: int, *, form: str = "plain", alpha: float = -1.0,
                  debug: bool = False, stream=None, torch_memory: bool = True,
-                 loop: str = "auto", tile_rows: int = 0):
+                 loop: str = "auto", tile_rows: int = 0, tuning_file: str | None = None):
         torch = _torch()
         self.lib = _lib.load()
         self.device = torch.cuda.current_device()
@@ -83,6 +84,8 @@ class Inpainter:
         opt.search_alpha = float(alpha)
         opt.loop_mode = LOOPS[loop]
         opt.tile_rows = int(tile_rows)
+        self._tf = tuning_file.encode() if tuning_file else None
+        opt.tuning_file = self._tf
         if self._alloc is not None:
             opt.dev_alloc = self._alloc.alloc
             opt.dev_free = self._alloc.free
@@ -187,6 +190,14 @@ class Inpainter:
         _check(self.lib.inpaint_loop_timing(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
                "inpaint_loop_timing")
         return a.value, b.value, n.value
+
+    def time_search(self, form: str = "plain", reps: int = 20):
+        """Isolated timing of one search of `form` for the current target:
+        (ms per search, best key (SSD << 32 | idx), evaluations)."""
+        ms, key, ev = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self.lib.inpaint_time_search(self.ctx, FORMS[form], int(reps), ctypes.byref(ms), ctypes.byref(key),
+                                            ctypes.byref(ev)), "inpaint_time_search")
+        return ms.value, key.value, ev.value
 
     def search_rect(self):
         v = [ctypes.c_int() for _ in range(4)]

@@ -34,8 +34,8 @@ cudaError_t launch_prio_init_fast(const ImgState& s, cudaStream_t st) {
 }
 
 // TMA descriptor of an image's RGBA words: 2-D (W, H), row pitch in bytes,
-// box (128 + 2r rounded up to 4) x (16 * srw + 2r); out-of-image reads give 0.
-int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out) {
+// box box_w x box_h words; out-of-image reads give 0.
+int make_image_tmap_box(const ImgState& s, int box_w, int box_h, CUtensorMap* out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -48,13 +48,17 @@ int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out) {
   }
   const cuuint64_t dims[2] = {(cuuint64_t)s.W, (cuuint64_t)s.H};
   const cuuint64_t strides[1] = {(cuuint64_t)s.pitch * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)((128 + 2 * s.r + 3) & ~3),
-                             (cuuint32_t)(kEngWarps * srw + 2 * s.r)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, s.img, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+// The engine's search window: (128 + 2r rounded up to 4) x (16 * srw + 2r).
+int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out) {
+  return make_image_tmap_box(s, (128 + 2 * s.r + 3) & ~3, kEngWarps * srw + 2 * s.r, out);
 }
 
 }  // namespace inp

@@ -414,6 +414,10 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
     return fail(INPAINT_ERR_NOMEM);
   }
   if (prepare_search_plain(r) != cudaSuccess) return fail(INPAINT_ERR_CUDA);
+  if (o.form == INPAINT_FORM_TC && encode_search_tc(s, &c->tc) != cudaSuccess) {
+    g_last_error = "tensor-core search: TMA descriptor encoding failed";
+    return fail(INPAINT_ERR_CUDA);
+  }
   {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || !(s.dtab = data_term_table(dev)))
@@ -614,6 +618,68 @@ int inpaint_info(const inpaint_ctx* c, int* width, int* height, int* patch_radiu
   if (patch_radius) *patch_radius = c->r;
   if (remaining) *remaining = c->h_ctrl->remaining;
   if (evals) *evals = c->h_ctrl->evals;
+  return INPAINT_OK;
+}
+
+int inpaint_time_search(inpaint_ctx* c, int form, int reps, double* ms_per_search,
+                        unsigned long long* best_key, unsigned long long* evals) {
+  if (!c || reps < 1 || !ms_per_search || (form != INPAINT_FORM_PLAIN && form != INPAINT_FORM_TC))
+    return INPAINT_ERR_ARG;
+  if (form == INPAINT_FORM_TC && c->r > 8) return INPAINT_ERR_UNSUPPORTED;
+  int rc = read_ctrl(c);
+  if (rc) return rc;
+  const Ctrl h = *c->h_ctrl;
+  if (h.status != 0) return h.status;
+  if (h.remaining <= 0 || h.px < 0) return INPAINT_DONE;
+  ImgState s = c->st;
+  TcPlan plan{};
+  if (form == INPAINT_FORM_TC) {
+    CK(prepare_search_tc(s, &plan));
+    CK(encode_search_tc(s, &plan));
+    s.n_partial = plan.grid;
+  } else {
+    CK(prepare_search_plain(s.r));
+    const dim3 g = search_plain_grid(s);
+    s.n_partial = (int)(g.x * g.y);
+  }
+  if (s.n_partial <= 0) return INPAINT_DONE;
+  unsigned long long* part = nullptr;
+  CK(cudaMalloc(&part, sizeof(unsigned long long) * s.n_partial));
+  s.partial = part;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto launch = [&]() {
+    return form == INPAINT_FORM_TC ? launch_search_tc(s, plan, c->stream) : launch_search_plain(s, c->stream);
+  };
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  std::vector<unsigned long long> keys(s.n_partial);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(keys.data(), part, sizeof(unsigned long long) * keys.size(), cudaMemcpyDeviceToHost);
+  // known pixels of the target patch
+  const int r = c->r, P = 2 * r + 1;
+  std::vector<uint8_t> om((size_t)P * P, 1);
+  const int x0 = std::max(0, h.px - r), x1 = std::min(c->W - 1, h.px + r);
+  const int y0 = std::max(0, h.py - r), y1 = std::min(c->H - 1, h.py + r);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(om.data(), P, s.omega + (size_t)y0 * c->W + x0, c->W, x1 - x0 + 1, y1 - y0 + 1,
+                     cudaMemcpyDeviceToHost);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(part);
+  CK(e);
+  long long n_known = 0;
+  for (int y = 0; y <= y1 - y0; ++y)
+    for (int x = 0; x <= x1 - x0; ++x) n_known += om[(size_t)y * P + x] == 0;
+  *ms_per_search = (double)ms / reps;
+  if (best_key) *best_key = *std::min_element(keys.begin(), keys.end());
+  if (evals) *evals = (unsigned long long)n_known * (unsigned long long)std::max(h.n_valid, 0);
   return INPAINT_OK;
 }
 

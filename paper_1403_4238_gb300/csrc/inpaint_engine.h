@@ -77,6 +77,7 @@ const EngineFns* engine_fns(int r);
 cudaError_t engine_occupancy(size_t smem, int* blocks_per_sm);
 cudaError_t engine_launch(size_t smem, const EngineArgs& ea, int grid, cudaStream_t st);
 int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out);
+int make_image_tmap_box(const ImgState& s, int box_w, int box_h, CUtensorMap* out);
 cudaError_t launch_update_fast(const ImgState& s, unsigned long long cond, int use_cond,
                                cudaStream_t st);
 

@@ -19,6 +19,7 @@
 //   ctrl   Ctrl          loop control block (selected p^, counters, status)
 //   trace  inpaint_step_info[trace_cap]   one record per iteration
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -366,9 +367,14 @@ dim3 search_plain_grid(const ImgState& s);
 // Tensor-core search (search_tc.cu), patch radius 1..8: a persistent grid over
 // tiles of 8 candidate rows; one partial key per CTA (grid partials).
 struct TcPlan {
-  int grid = 0, nx = 0, ntiles = 0, smem = 0;
+  int grid = 0, nx = 0, ntiles = 0, smem = 0, tmap_rows = 0;
+  bool tmap_ready = false;
+  CUtensorMap tmap;  // RGBA words, box 256 x tmap_rows (set by encode_search_tc)
 };
+// Geometry and launch shape (needs the search rectangle, not the buffers).
 cudaError_t prepare_search_tc(const ImgState& s, TcPlan* plan);
+// TMA descriptor of s.img: call once the image buffer exists.
+cudaError_t encode_search_tc(const ImgState& s, TcPlan* plan);
 cudaError_t launch_search_tc(const ImgState& s, const TcPlan& plan, cudaStream_t st);
 cudaError_t launch_update(const ImgState& s, int do_fill, unsigned long long cond_handle,
                           int use_cond, cudaStream_t st);

@@ -25,26 +25,29 @@
 //    starts.  One MMA per (rho, K chunk, plane) updates all RP row pairs; B
 //    for rho + 2 is B for rho shifted by one 8-row group, so one strip of
 //    groups per (plane, K chunk, parity of rho) serves every rho.
-// A tile is kTcRows candidate rows x TS candidate columns; its planes
-// (R', G', B', hi, lo as BF16, 512 columns each) are converted from the RGBA
-// image into shared memory, one elected thread issues the MMAs, and the
-// eight warps read the accumulators back (tcgen05.ld), add the validity test
-// (count map) and reduce to one (SSD << 32 | idx) key per CTA.
-#include "inpaint_internal.cuh"
+// A tile is RC candidate rows x TS candidate columns.  Per CTA the tiles
+// run as a pipeline: one control warp issues the TMA load of tile i+1's RGBA
+// rows into a staging buffer and the MMAs of tile i into one of two tensor-
+// memory accumulator sets, while eight worker warps read the accumulators
+// of tile i-1 back (tcgen05.ld), apply the validity test (count map) and
+// keep the smallest (SSD << 32 | idx) key; the workers then convert the
+// staged words of tile i+1 into the five BF16 planes (R', G', B', hi, lo).
+#include "inpaint_engine.h"
 #include "ptx.cuh"
 
 namespace inp {
 namespace {
 
-constexpr int kTcThreads = 256;
-constexpr int kTcRows = 8;      // candidate rows per tile
-constexpr int kTcPlaneW = 512;  // plane row length (BF16 elements)
+constexpr int kTcWorkers = 8;                       // worker warps
+constexpr int kTcThreads = 32 * (kTcWorkers + 1);   // + the control warp
+constexpr int kTcPlaneW = 512;                      // plane row (BF16 elements)
+constexpr int kTcMinSmem = 100 * 1024;  // at most two CTAs (2 x 256 TMEM columns) per SM
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
 template <int R>
 struct TcGeom {
   static constexpr int P = 2 * R + 1;
-  static constexpr int RC = kTcRows;
+  static constexpr int RC = R == 8 ? 4 : 8;            // candidate rows per tile
   static constexpr int RP = RC / 2;                    // candidate row pairs
   static constexpr int N = 8 * RP;                     // MMA N
   static constexpr int KC = (P + 22) / 16;             // K chunks: taps j = b + dx < P + 7
@@ -53,15 +56,21 @@ struct TcGeom {
   static constexpr int TMAX = (NRHO - 1) / 2;
   static constexpr int GB = TMAX + RP;                 // 8-row groups per B strip
   static constexpr int TS = (kTcPlaneW + 1 - P) & ~7;  // candidate columns per tile
+  static constexpr int STG_BYTES = 2 * NR * 256 * 4;   // two 256-word TMA boxes
   static constexpr int PLANE_BYTES = NR * kTcPlaneW * 2 + 128;
   static constexpr int B_BYTES = 4 * KC * 2 * GB * 256;
-  static constexpr int OFF_B = 5 * PLANE_BYTES;
+  static constexpr int OFF_PL = STG_BYTES;
+  static constexpr int OFF_B = OFF_PL + 5 * PLANE_BYTES;
   static constexpr int OFF_T = OFF_B + B_BYTES;  // int16 T[4][P * P]
   static constexpr int OFF_MISC = (OFF_T + 4 * P * P * 2 + 15) & ~15;
-  static constexpr int SMEM = OFF_MISC + 16 + 32 * 8 + 128;  // + base alignment
-  static constexpr uint32_t TMEM_COLS = 3 * N <= 32 ? 32 : 3 * N <= 64 ? 64 : 3 * N <= 128 ? 128 : 256;
-  static_assert(RP % 2 == 0 && N % 16 == 0 && N <= 256, "M = 128 needs N a multiple of 16");
+  static constexpr int RAW = OFF_MISC + 384 + 128;  // + base alignment
+  static constexpr int SMEM = RAW < kTcMinSmem ? kTcMinSmem : RAW;
+  static constexpr uint32_t ACC = 3 * N;             // columns of one accumulator set
+  static constexpr uint32_t TMEM_COLS = 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128 : 256;
+  static_assert(RP % 2 == 0 || RP == 2, "row pairs split over two warp halves");
+  static_assert(N % 16 == 0 && N <= 256, "M = 128 needs N a multiple of 16");
   static_assert(KC * 16 >= P + 7, "K chunks must cover every tap");
+  static_assert(2 * ACC <= 256, "two accumulator sets in 256 columns");
   static_assert(SMEM <= 227 * 1024, "tile does not fit in shared memory");
 };
 
@@ -164,22 +173,52 @@ __device__ inline void convert8(const uint4& v0, const uint4& v1, uint4 (&o)[5])
 }
 
 template <int R>
-__global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, int ntiles) {
+struct TcTile {
+  int x0, y0;
+  __device__ TcTile(const ImgState& s, int tile, int nx) {
+    x0 = ((s.cx0 - R) & ~7) + (tile % nx) * TcGeom<R>::TS;
+    y0 = s.cy0 - R + (tile / nx) * TcGeom<R>::RC;
+  }
+};
+
+template <int R>
+__global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, int ntiles,
+                                                          const __grid_constant__ CUtensorMap tmap) {
   using G = TcGeom<R>;
   constexpr int P = G::P;
   extern __shared__ __align__(16) uint8_t tc_dyn[];
   const Ctrl* c = s.ctrl;
   if (!loop_active(c)) return;
   uint8_t* sm = tc_dyn + ((128u - (smem_addr(tc_dyn) & 127u)) & 127u);
+  const uint32_t* stg = reinterpret_cast<const uint32_t*>(sm);
   int16_t* tv = reinterpret_cast<int16_t*>(sm + G::OFF_T);
-  uint16_t* bsm = reinterpret_cast<uint16_t*>(sm + G::OFF_B);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + G::OFF_MISC);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + G::OFF_MISC + 8);
-  int* a2_slot = reinterpret_cast<int*>(sm + G::OFF_MISC + 12);
-  unsigned long long* red = reinterpret_cast<unsigned long long*>(sm + G::OFF_MISC + 16);
+  uint64_t* stg_bar = reinterpret_cast<uint64_t*>(sm + G::OFF_MISC);
+  uint64_t* mma_bar = stg_bar + 1;  // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + G::OFF_MISC + 24);
+  int* a2_slot = reinterpret_cast<int*>(sm + G::OFF_MISC + 28);
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(sm + G::OFF_MISC + 32);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool ctl = warp == kTcWorkers, ctl0 = ctl && lane == 0;
   const int px = c->px, py = c->py;
+  int tma_n = 0, mma_n[2] = {0, 0};  // operations issued (control lane)
 
+  auto issue_tma = [&](int tile) {
+    const TcTile<R> t(s, tile, nx);
+    const bool two = t.x0 + 256 < s.W;  // the right box lies (partly) inside the image
+    mbar_expect_tx(stg_bar, (uint32_t)((two ? 2 : 1) * G::NR * 256 * 4));
+    tma_load_2d(sm, &tmap, t.x0, t.y0, stg_bar);
+    if (two) tma_load_2d(sm + G::NR * 256 * 4, &tmap, t.x0 + 256, t.y0, stg_bar);
+    ++tma_n;
+  };
+
+  if (ctl0) {
+    mbar_init(stg_bar, 1);
+    mbar_init(mma_bar, 1);
+    mbar_init(mma_bar + 1, 1);
+    fence_mbar_init();
+    if ((int)blockIdx.x < ntiles) issue_tma(blockIdx.x);
+  }
+  if (warp == 0) tc_alloc(tmem_slot, G::TMEM_COLS);
   // Target patch: shifted values and the known indicator, T[kappa][dy * P + dx].
   for (int i = tid; i < P * P; i += kTcThreads) {
     const int dy = i / P, dx = i - dy * P;
@@ -199,32 +238,35 @@ __global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, in
   }
   // Zero the tails behind the planes (read only by discarded candidates).
   for (int i = tid; i < 5 * 32; i += kTcThreads)
-    reinterpret_cast<uint32_t*>(sm + (i / 32) * G::PLANE_BYTES + G::NR * kTcPlaneW * 2)[i % 32] = 0u;
-  if (tid == 0) {
-    mbar_init(mbar, 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) tc_alloc(tmem_slot, G::TMEM_COLS);
+    reinterpret_cast<uint32_t*>(sm + G::OFF_PL + (i / 32) * G::PLANE_BYTES +
+                                G::NR * kTcPlaneW * 2)[i % 32] = 0u;
   __syncthreads();
 
-  // B strips: element e = (((kappa * KC + kc) * 2 + par) * GB + gi) * 128 + w;
-  // w = core matrix cm (K half), row b, column jj.
-  constexpr int NB = 4 * G::KC * 2 * G::GB * 128;
-  for (int e = tid; e < NB; e += kTcThreads) {
-    int rem = e;
-    const int w = rem & 127;
-    rem >>= 7;
-    const int gi = rem % G::GB;
-    rem /= G::GB;
-    const int par = rem & 1;
-    rem >>= 1;
-    const int kc = rem % G::KC, kap = rem / G::KC;
-    const int cm = w >> 6, b = (w >> 3) & 7, jj = w & 7;
+  // B strips, one 16-byte core-matrix row per step: row rr of strip
+  // ((kappa * KC + kc) * 2 + par), group gi, core matrix cm (K half), row b.
+  constexpr int NBR = 4 * G::KC * 2 * G::GB * 16;
+  for (int rr = tid; rr < NBR; rr += kTcThreads) {
+    const int b = rr & 7, cm = (rr >> 3) & 1;
+    int rest = rr >> 4;
+    const int gi = rest % G::GB;
+    rest /= G::GB;
+    const int par = rest & 1;
+    rest >>= 1;
+    const int kc = rest % G::KC, kap = rest / G::KC;
     const int dy = par - 2 * (gi - G::TMAX);
-    const int dx = 16 * kc + 8 * cm + jj - b;
-    int v = 0;
-    if (dy >= 0 && dy < P && dx >= 0 && dx < P) v = tv[kap * P * P + dy * P + dx];
-    bsm[e] = (uint16_t)bf16_int(v);
+    uint32_t wv[4] = {0u, 0u, 0u, 0u};
+    if (dy >= 0 && dy < P) {
+      const int dx0 = 16 * kc + 8 * cm - b;
+      const int16_t* trow = tv + kap * P * P + dy * P;
+#pragma unroll
+      for (int jj = 0; jj < 8; jj += 2) {
+        const int d0 = dx0 + jj, d1 = d0 + 1;
+        const int v0 = (d0 >= 0 && d0 < P) ? trow[d0] : 0;
+        const int v1 = (d1 >= 0 && d1 < P) ? trow[d1] : 0;
+        wv[jj >> 1] = bf16_int(v0) | (bf16_int(v1) << 16);
+      }
+    }
+    *reinterpret_cast<uint4*>(sm + G::OFF_B + rr * 16) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
   if (warp == 0) {
     int a2 = 0;
@@ -237,102 +279,122 @@ __global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, in
     if (lane == 0) *a2_slot = a2;
   }
   fence_proxy_async_smem();
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int a2 = *a2_slot;
-  const uint32_t plane0 = smem_addr(sm), b0 = smem_addr(sm + G::OFF_B);
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(G::N >> 3) << 17) |
                          ((uint32_t)(128 >> 4) << 24);
-  const int xb = (s.cx0 - R) & ~7, ys = s.cy0 - R;
+  const uint64_t adesc0 = tc_desc(smem_addr(sm + G::OFF_PL), 16, 128);
+  const uint64_t bdesc0 = tc_desc(smem_addr(sm + G::OFF_B), 128, 256);
   const int wq = warp & 3, kh = warp >> 2;
   const int a = 32 * wq + lane, a_row = a >> 6, a_blk = a & 63;
   unsigned long long best = ~0ull;
-  uint32_t phase = 0;
-  bool failed = false;
+  int bad = 0;
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int x0 = xb + (tile % nx) * G::TS, y0 = ys + (tile / nx) * G::RC;
-    // planes of rows y0 .. y0 + NR - 1, columns x0 .. x0 + 511
-    for (int g = tid; g < G::NR * 64; g += kTcThreads) {
-      const int row = g >> 6, cg = g & 63;
-      const int y = y0 + row, x = x0 + 8 * cg;
-      uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
-      if (y < s.H) {
-        const uint4* src = reinterpret_cast<const uint4*>(s.img + (size_t)y * s.pitch + x);
-        if (x < s.pitch) v0 = __ldg(src);
-        if (x + 4 < s.pitch) v1 = __ldg(src + 1);
-      }
-      uint4 o[5];
-      convert8(v0, v1, o);
+  for (int i = 0;; ++i) {
+    const int tile = blockIdx.x + i * gridDim.x;
+    const bool has = tile < ntiles;
+    if (has && !ctl) {
+      // staged words of this tile -> planes
+      if (!mbar_wait(stg_bar, (uint32_t)(i & 1), kTcWaitNs)) {
+        bad = 1;
+      } else {
+        for (int g = tid; g < G::NR * 64; g += 32 * kTcWorkers) {
+          const int row = g >> 6, cg = g & 63;
+          const uint4* src = reinterpret_cast<const uint4*>(
+              stg + ((cg >> 5) * G::NR + row) * 256 + (cg & 31) * 8);
+          uint4 o[5];
+          convert8(src[0], src[1], o);
 #pragma unroll
-      for (int p = 0; p < 5; ++p)
-        *reinterpret_cast<uint4*>(sm + p * G::PLANE_BYTES + row * (kTcPlaneW * 2) + 16 * cg) = o[p];
-    }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      for (int rho = 0; rho < G::NRHO; ++rho) {
-        const int par = rho & 1, t = rho >> 1;
-        for (int kc = 0; kc < G::KC; ++kc) {
-          const uint32_t aoff = (uint32_t)(rho * kTcPlaneW * 2 + 32 * kc);
-          const uint32_t boff = (uint32_t)((G::TMAX - t) * 256);
-          const uint32_t first = (rho == 0 && kc == 0) ? 1u : 0u;
-#pragma unroll
-          for (int ch = 0; ch < 3; ++ch) {
-            const uint64_t ad = tc_desc(plane0 + ch * G::PLANE_BYTES + aoff, 16, 128);
-            const uint64_t bd =
-                tc_desc(b0 + ((ch * G::KC + kc) * 2 + par) * G::GB * 256 + boff, 128, 256);
-            tc_mma(tmem, ad, bd, idesc, (first && ch == 0) ? 0u : 1u);
-          }
-          const uint64_t bm = tc_desc(b0 + ((3 * G::KC + kc) * 2 + par) * G::GB * 256 + boff, 128, 256);
-          tc_mma(tmem + G::N, tc_desc(plane0 + 3 * G::PLANE_BYTES + aoff, 16, 128), bm, idesc,
-                 first ? 0u : 1u);
-          tc_mma(tmem + 2 * G::N, tc_desc(plane0 + 4 * G::PLANE_BYTES + aoff, 16, 128), bm, idesc,
-                 first ? 0u : 1u);
+          for (int p = 0; p < 5; ++p)
+            *reinterpret_cast<uint4*>(sm + G::OFF_PL + p * G::PLANE_BYTES + row * (kTcPlaneW * 2) +
+                                      16 * cg) = o[p];
         }
       }
-      tc_commit(mbar);
-    }
-    const bool got = mbar_wait(mbar, phase, kTcWaitNs);
-    phase ^= 1u;
-    if (__syncthreads_or(!got)) {
-      failed = true;
-      break;
-    }
-    tc_fence_after();
-#pragma unroll
-    for (int kk = 0; kk < G::RP / 2; ++kk) {
-      const int k = kh * (G::RP / 2) + kk;
-      uint32_t X[8], Hv[8], Lv[8];
-      const uint32_t ta = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(8 * k);
-      tc_ld8(ta, X);
-      tc_ld8(ta + G::N, Hv);
-      tc_ld8(ta + 2 * G::N, Lv);
-      tc_wait_ld();
-      const int qy = y0 + 2 * k + a_row + R;
-      if (qy > s.cy1) continue;
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const int u = 8 * a_blk + b, qx = x0 + u + R;
-        if (u >= G::TS || qx < s.cx0 || qx > s.cx1) continue;
-        const int xv = __float2int_rn(__uint_as_float(X[b]));
-        const int hv = __float2int_rn(__uint_as_float(Hv[b]));
-        const int lv = __float2int_rn(__uint_as_float(Lv[b]));
-        const uint32_t ssd = (uint32_t)(a2 - 2 * xv + 256 * hv + lv);
-        const int idx = qy * s.W + qx;
-        const unsigned long long key = ((unsigned long long)ssd << 32) | (unsigned)idx;
-        if (key < best && s.count[idx] == 0) best = key;
-      }
+      fence_proxy_async_smem();
     }
     tc_fence_before();
+    if (__syncthreads_or(bad)) break;
+    if (ctl) {
+      if (lane == 0 && has) {
+        tc_fence_after();
+        if (tile + (int)gridDim.x < ntiles) issue_tma(tile + gridDim.x);
+        const uint32_t dcol = tmem + (uint32_t)((i & 1) * G::ACC);
+#pragma unroll 1
+        for (int rho = 0; rho < G::NRHO; ++rho) {
+          const int par = rho & 1, t = rho >> 1;
+#pragma unroll
+          for (int kc = 0; kc < G::KC; ++kc) {
+            const uint64_t ad = adesc0 + (uint64_t)(rho * (kTcPlaneW * 2 / 16) + 2 * kc);
+            const uint32_t first = (rho == 0 && kc == 0) ? 1u : 0u;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+              const uint64_t bd =
+                  bdesc0 + (uint64_t)((((ch * G::KC + kc) * 2 + par) * G::GB + G::TMAX - t) * 16);
+              tc_mma(dcol, ad + (uint64_t)(ch * (G::PLANE_BYTES / 16)), bd, idesc,
+                     (first && ch == 0) ? 0u : 1u);
+            }
+            const uint64_t bm =
+                bdesc0 + (uint64_t)((((3 * G::KC + kc) * 2 + par) * G::GB + G::TMAX - t) * 16);
+            tc_mma(dcol + G::N, ad + (uint64_t)(3 * (G::PLANE_BYTES / 16)), bm, idesc, first ? 0u : 1u);
+            tc_mma(dcol + 2 * G::N, ad + (uint64_t)(4 * (G::PLANE_BYTES / 16)), bm, idesc,
+                   first ? 0u : 1u);
+          }
+        }
+        tc_commit(mma_bar + (i & 1));
+        ++mma_n[i & 1];
+      }
+      __syncwarp();
+    } else if (i > 0) {
+      // accumulators of the previous tile (its MMAs completed: waited below)
+      const TcTile<R> t(s, tile - gridDim.x, nx);
+      const uint32_t buf = (uint32_t)(((i - 1) & 1) * G::ACC);
+#pragma unroll
+      for (int kk = 0; kk < G::RP / 2; ++kk) {
+        const int k = kh * (G::RP / 2) + kk;
+        uint32_t X[8], Hv[8], Lv[8];
+        const uint32_t ta = tmem + ((uint32_t)(32 * wq) << 16) + buf + (uint32_t)(8 * k);
+        tc_ld8(ta, X);
+        tc_ld8(ta + G::N, Hv);
+        tc_ld8(ta + 2 * G::N, Lv);
+        tc_wait_ld();
+        const int qy = t.y0 + 2 * k + a_row + R;
+        if (qy > s.cy1) continue;
+        unsigned long long key[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int u = 8 * a_blk + b, qx = t.x0 + u + R;
+          const int xv = __float2int_rn(__uint_as_float(X[b]));
+          const int hv = __float2int_rn(__uint_as_float(Hv[b]));
+          const int lv = __float2int_rn(__uint_as_float(Lv[b]));
+          const uint32_t ssd = (uint32_t)(a2 - 2 * xv + 256 * hv + lv);
+          key[b] = (u < G::TS && qx >= s.cx0 && qx <= s.cx1)
+                       ? (((unsigned long long)ssd << 32) | (unsigned)(qy * s.W + qx))
+                       : ~0ull;
+        }
+        int cnt[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) cnt[b] = key[b] < best ? s.count[(unsigned)key[b]] : 1;
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+          if (cnt[b] == 0 && key[b] < best) best = key[b];
+      }
+    }
+    if (!has) break;
+    // this tile's MMAs must finish before its planes are overwritten
+    if (!mbar_wait(mma_bar + (i & 1), (uint32_t)((i >> 1) & 1), kTcWaitNs)) bad = 1;
+    tc_fence_after();
   }
 
-  if (failed) {
+  if (bad) {
     if (tid == 0) atomicCAS(const_cast<int*>(&c->status), 0, INPAINT_ERR_TIMEOUT);
-    // let the MMAs in flight finish (bounded) before the accumulators are freed
-    mbar_wait(mbar, phase ^ 1u, kTcWaitNs);
+    if (ctl0) {  // let the copies and MMAs in flight finish (bounded) before freeing
+      if (tma_n) mbar_wait(stg_bar, (uint32_t)((tma_n - 1) & 1), kTcWaitNs);
+      for (int j = 0; j < 2; ++j)
+        if (mma_n[j]) mbar_wait(mma_bar + j, (uint32_t)((mma_n[j] - 1) & 1), kTcWaitNs);
+    }
   }
   best = block_min_u64(best, red);
   if (tid == 0) s.partial[blockIdx.x] = best;
@@ -357,19 +419,21 @@ cudaError_t prepare_r(const ImgState& s, TcPlan* plan) {
       cudaSuccess)
     return e;
   if (bps < 1) return cudaErrorInvalidConfiguration;
-  if (bps > 2) bps = 2;  // at most 2 x 256 tensor-memory columns per SM
+  if (bps > 2) bps = 2;
   const int xb = (s.cx0 - R) & ~7;
   plan->nx = s.cx1 < s.cx0 ? 0 : (s.cx1 - R - xb) / G::TS + 1;
   const int ny = s.cy1 < s.cy0 ? 0 : (s.cy1 - s.cy0) / G::RC + 1;
   plan->ntiles = plan->nx * ny;
   plan->grid = plan->ntiles < sms * bps ? plan->ntiles : sms * bps;
   plan->smem = G::SMEM;
+  plan->tmap_rows = G::NR;
+  plan->tmap_ready = false;
   return cudaSuccess;
 }
 
 template <int R>
 cudaError_t launch_r(const ImgState& s, const TcPlan& p, cudaStream_t st) {
-  k_search_tc<R><<<p.grid, kTcThreads, p.smem, st>>>(s, p.nx, p.ntiles);
+  k_search_tc<R><<<p.grid, kTcThreads, p.smem, st>>>(s, p.nx, p.ntiles, p.tmap);
   return cudaGetLastError();
 }
 
@@ -389,8 +453,16 @@ cudaError_t prepare_search_tc(const ImgState& s, TcPlan* plan) {
   }
 }
 
+cudaError_t encode_search_tc(const ImgState& s, TcPlan* plan) {
+  if (!s.img || plan->tmap_rows <= 0) return cudaErrorInvalidValue;
+  if (make_image_tmap_box(s, 256, plan->tmap_rows, &plan->tmap) != 0) return cudaErrorInvalidValue;
+  plan->tmap_ready = true;
+  return cudaSuccess;
+}
+
 cudaError_t launch_search_tc(const ImgState& s, const TcPlan& p, cudaStream_t st) {
   if (p.grid <= 0) return cudaSuccess;
+  if (!p.tmap_ready) return cudaErrorInvalidValue;
   switch (s.r) {
     case 1: return launch_r<1>(s, p, st);
     case 2: return launch_r<2>(s, p, st);

@@ -80,12 +80,19 @@ def ellipse_mask(W: int, H: int, n: int, lo: float, hi: float, seed: int) -> np.
     ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
 
     def build(scale):
+        # each ellipse is evaluated on its bounding box only (plus a margin);
+        # pixels outside it are farther than scale * max(ax, ay) from the centre
         m = np.zeros((H, W), bool)
         for i in range(n):
-            dx, dy = xs - cx[i], ys - cy[i]
+            ext = scale * max(ax[i], ay[i]) + 2.0
+            x0, x1 = max(0, int(cx[i] - ext)), min(W, int(cx[i] + ext) + 2)
+            y0, y1 = max(0, int(cy[i] - ext)), min(H, int(cy[i] + ext) + 2)
+            if x0 >= x1 or y0 >= y1:
+                continue
+            dx, dy = xs[y0:y1, x0:x1] - cx[i], ys[y0:y1, x0:x1] - cy[i]
             u = dx * math.cos(rot[i]) + dy * math.sin(rot[i])
             v = -dx * math.sin(rot[i]) + dy * math.cos(rot[i])
-            m |= (u / (scale * ax[i])) ** 2 + (v / (scale * ay[i])) ** 2 <= 1.0
+            m[y0:y1, x0:x1] |= (u / (scale * ax[i])) ** 2 + (v / (scale * ay[i])) ** 2 <= 1.0
         return m
 
     a, b = 0.5, 0.5 * math.hypot(W, H)
