@@ -388,11 +388,9 @@ def main():
             ms.append(ev[0].elapsed_time(ev[2]))
             run_ms.append(ev[1].elapsed_time(ev[2]))
     torch.cuda.synchronize()
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_1403_4238_gb300.dist import max_over_ranks
+
+    total_ms = max_over_ranks(sum(ms))
     value = evals_per_removal * args.steps * world / (total_ms / 1e3)
     plain_out = ip.result()
     search_ns, update_ns, timed_iters = ip.loop_timing()
