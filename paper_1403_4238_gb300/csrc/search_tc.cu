@@ -38,7 +38,7 @@
 namespace inp {
 namespace {
 
-constexpr int kTcWorkers = 8;                       // worker warps
+constexpr int kTcWorkers = 16;                      // worker warps
 constexpr int kTcThreads = 32 * (kTcWorkers + 1);   // + the control warp
 constexpr int kTcPlaneW = 512;                      // plane row (BF16 elements)
 constexpr int kTcMinSmem = 100 * 1024;  // at most two CTAs (2 x 256 TMEM columns) per SM
@@ -67,7 +67,7 @@ struct TcGeom {
   static constexpr int SMEM = RAW < kTcMinSmem ? kTcMinSmem : RAW;
   static constexpr uint32_t ACC = 3 * N;             // columns of one accumulator set
   static constexpr uint32_t TMEM_COLS = 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128 : 256;
-  static_assert(RP % 2 == 0 || RP == 2, "row pairs split over two warp halves");
+  static_assert(RP <= 8, "at most two row pairs per worker warp");
   static_assert(N % 16 == 0 && N <= 256, "M = 128 needs N a multiple of 16");
   static_assert(KC * 16 >= P + 7, "K chunks must cover every tap");
   static_assert(2 * ACC <= 256, "two accumulator sets in 256 columns");
@@ -182,7 +182,7 @@ struct TcTile {
 };
 
 template <int R>
-__global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, int ntiles,
+__global__ void __launch_bounds__(kTcThreads, 1) k_search_tc(ImgState s, int nx, int ntiles,
                                                           const __grid_constant__ CUtensorMap tmap) {
   using G = TcGeom<R>;
   constexpr int P = G::P;
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, in
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool ctl = warp == kTcWorkers, ctl0 = ctl && lane == 0;
   const int px = c->px, py = c->py;
-  int tma_n = 0, mma_n[2] = {0, 0};  // operations issued (control lane)
+  int tma_n = 0, mma_n0 = 0, mma_n1 = 0;  // operations issued (control lane)
 
   auto issue_tma = [&](int tile) {
     const TcTile<R> t(s, tile, nx);
@@ -288,19 +288,39 @@ __global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, in
                          ((uint32_t)(128 >> 4) << 24);
   const uint64_t adesc0 = tc_desc(smem_addr(sm + G::OFF_PL), 16, 128);
   const uint64_t bdesc0 = tc_desc(smem_addr(sm + G::OFF_B), 128, 256);
-  const int wq = warp & 3, kh = warp >> 2;
+  const int wq = warp & 3, kh = warp >> 2;  // TMEM lane quarter; row pairs kh, kh + 4, ...
   const int a = 32 * wq + lane, a_row = a >> 6, a_blk = a & 63;
+  constexpr int KPW = (G::RP + 3) / 4;  // row pairs per worker warp
   unsigned long long best = ~0ull;
   int bad = 0;
 
   for (int i = 0;; ++i) {
     const int tile = blockIdx.x + i * gridDim.x;
     const bool has = tile < ntiles;
+    // validity counts of the previous tile's candidates, loaded before the
+    // conversion so that their latency is hidden behind it
+    int cnt[KPW][8];
+    if (!ctl && i > 0) {
+      const TcTile<R> t(s, tile - gridDim.x, nx);
+#pragma unroll
+      for (int kk = 0; kk < KPW; ++kk) {
+        const int k = kh + 4 * kk;
+        const int qy = t.y0 + 2 * k + a_row + R;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int u = 8 * a_blk + b, qx = t.x0 + u + R;
+          cnt[kk][b] = (k < G::RP && qy <= s.cy1 && u < G::TS && qx >= s.cx0 && qx <= s.cx1)
+                           ? __ldcg(&s.count[(size_t)qy * s.W + qx])
+                           : 1;
+        }
+      }
+    }
     if (has && !ctl) {
       // staged words of this tile -> planes
       if (!mbar_wait(stg_bar, (uint32_t)(i & 1), kTcWaitNs)) {
         bad = 1;
       } else {
+#pragma unroll 2
         for (int g = tid; g < G::NR * 64; g += 32 * kTcWorkers) {
           const int row = g >> 6, cg = g & 63;
           const uint4* src = reinterpret_cast<const uint4*>(
@@ -344,7 +364,7 @@ __global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, in
           }
         }
         tc_commit(mma_bar + (i & 1));
-        ++mma_n[i & 1];
+        if (i & 1) ++mma_n1; else ++mma_n0;
       }
       __syncwarp();
     } else if (i > 0) {
@@ -352,8 +372,9 @@ __global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, in
       const TcTile<R> t(s, tile - gridDim.x, nx);
       const uint32_t buf = (uint32_t)(((i - 1) & 1) * G::ACC);
 #pragma unroll
-      for (int kk = 0; kk < G::RP / 2; ++kk) {
-        const int k = kh * (G::RP / 2) + kk;
+      for (int kk = 0; kk < KPW; ++kk) {
+        const int k = kh + 4 * kk;
+        if (k >= G::RP) break;  // warp-uniform
         uint32_t X[8], Hv[8], Lv[8];
         const uint32_t ta = tmem + ((uint32_t)(32 * wq) << 16) + buf + (uint32_t)(8 * k);
         tc_ld8(ta, X);
@@ -361,25 +382,16 @@ __global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, in
         tc_ld8(ta + 2 * G::N, Lv);
         tc_wait_ld();
         const int qy = t.y0 + 2 * k + a_row + R;
-        if (qy > s.cy1) continue;
-        unsigned long long key[8];
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-          const int u = 8 * a_blk + b, qx = t.x0 + u + R;
+          const int qx = t.x0 + 8 * a_blk + b + R;
           const int xv = __float2int_rn(__uint_as_float(X[b]));
           const int hv = __float2int_rn(__uint_as_float(Hv[b]));
           const int lv = __float2int_rn(__uint_as_float(Lv[b]));
           const uint32_t ssd = (uint32_t)(a2 - 2 * xv + 256 * hv + lv);
-          key[b] = (u < G::TS && qx >= s.cx0 && qx <= s.cx1)
-                       ? (((unsigned long long)ssd << 32) | (unsigned)(qy * s.W + qx))
-                       : ~0ull;
+          const unsigned long long key = ((unsigned long long)ssd << 32) | (unsigned)(qy * s.W + qx);
+          if (cnt[kk][b] == 0 && key < best) best = key;
         }
-        int cnt[8];
-#pragma unroll
-        for (int b = 0; b < 8; ++b) cnt[b] = key[b] < best ? s.count[(unsigned)key[b]] : 1;
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-          if (cnt[b] == 0 && key[b] < best) best = key[b];
       }
     }
     if (!has) break;
@@ -392,8 +404,8 @@ __global__ void __launch_bounds__(kTcThreads) k_search_tc(ImgState s, int nx, in
     if (tid == 0) atomicCAS(const_cast<int*>(&c->status), 0, INPAINT_ERR_TIMEOUT);
     if (ctl0) {  // let the copies and MMAs in flight finish (bounded) before freeing
       if (tma_n) mbar_wait(stg_bar, (uint32_t)((tma_n - 1) & 1), kTcWaitNs);
-      for (int j = 0; j < 2; ++j)
-        if (mma_n[j]) mbar_wait(mma_bar + j, (uint32_t)((mma_n[j] - 1) & 1), kTcWaitNs);
+      if (mma_n0) mbar_wait(mma_bar, (uint32_t)((mma_n0 - 1) & 1), kTcWaitNs);
+      if (mma_n1) mbar_wait(mma_bar + 1, (uint32_t)((mma_n1 - 1) & 1), kTcWaitNs);
     }
   }
   best = block_min_u64(best, red);
