@@ -108,6 +108,8 @@ __device__ inline void compute_rows(const uint32_t* __restrict__ stage, int row0
 
 struct EngSmemTail {
   uint64_t full[2];  // TMA completion barriers of the two stages
+  int bcur;          // first search batch of this CTA in the round
+  int bnx[2];        // next batch, written by thread 0 in alternate slots
   unsigned long long red64[32];
   int red32[32];
   int flag;
@@ -229,6 +231,11 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   const int ns = lead_searches ? tsize : min(tsize - 1, nbatch);
   const bool leader = rank == tsize - 1;
   const bool searcher = rank < ns;
+  // Batches [0, nst) go one per searcher (the leader, busy with the
+  // speculative phase first, takes none of them); the rest are handed out
+  // in arrival order from the team counter, so a CTA that starts late or
+  // runs slow takes fewer.
+  const int nst = min(nbatch, lead_searches && tsize > 1 ? ns - 1 : ns);
   const unsigned n_wait = (unsigned)(lead_searches ? ns - 1 : ns);
   bool resident = false;  // stage0 holds this CTA's only batch of the image
   if (tid == 0) {
@@ -241,8 +248,10 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
 
   // One search round for target (px, py): this CTA's batches; returns its
   // best key.  Whole block.
+  auto grab = [&]() -> int { return nst + (int)atomicAdd(&tc->next, 1u); };
   auto search_round = [&](int px, int py) -> unsigned long long {
-    const int b0 = rank;
+    const bool has_static = rank < nst && !(leader && lead_searches && tsize > 1);
+    const int b0 = has_static ? rank : nbatch;
     const bool need0 = !resident ||
                        (abs(prev_px - (xb + 128 * (b0 % max(ncg, 1)) + 64)) <= 64 + 2 * R + 4 &&
                         abs(prev_py - (s.cy0 + B * (b0 / max(ncg, 1)) + B / 2)) <= B / 2 + 2 * R + 1);
@@ -252,7 +261,10 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       mbar_expect_tx(bar, (uint32_t)(G::BW * G::BH * 4));
       tma_load_2d(st, map, xb - R + 128 * gx, s.cy0 + B * gy - R, bar);
     };
-    if (tid == 0 && b0 < nbatch && need0) issue(b0, stage0, &tl.full[0]);
+    if (tid == 0) {
+      tl.bcur = b0 < nbatch ? b0 : (nbatch > nst ? grab() : nbatch);
+      if (tl.bcur < nbatch && (tl.bcur != b0 || need0)) issue(tl.bcur, stage0, &tl.full[0]);
+    }
     // target patch: one thread per pixel, then the row masks
     if (tid < P * P) {
       const int tx = px + tid % P - R, ty = py + tid / P - R;
@@ -275,9 +287,13 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     unsigned long long best = ~0ull;
     int cur = 0;
     bool ok = true;
-    for (int b = b0; b < nbatch; b += ns) {
-      const int nb = b + ns;
-      if (tid == 0 && nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1]);
+    int nproc = 0;
+    for (int b = tl.bcur; b < nbatch;) {
+      if (tid == 0) {
+        const int nb = nbatch > nst ? grab() : nbatch;
+        tl.bnx[cur] = nb;  // read by all after the barrier at the end of this batch
+        if (nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1]);
+      }
       const int gx = b % ncg, gy = b / ncg;
       const int qx0 = xb + 128 * gx + lane * 4, qy0 = s.cy0 + B * gy + warp * SRW;
       int cnt[SRW][4];
@@ -304,19 +320,21 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
             const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
             best = key < best ? key : best;
           }
+      ++nproc;
       if (__syncthreads_or(!got)) {  // a bounded wait gave up: stop uniformly
         ok = false;
-        if (nb < nbatch) {
+        if (tl.bnx[cur] < nbatch) {
           mbar_wait(&tl.full[cur ^ 1], cur ? ph0 : ph1, limit);
           if (cur) ph0 ^= 1; else ph1 ^= 1;
         }
         break;
       }
+      b = tl.bnx[cur];
       cur ^= 1;
     }
-    // the tile stays resident when it is this CTA's only batch (the leader's
+    // the tile stays resident when it was this CTA's only batch (the leader's
     // shared memory is reused by its update phase)
-    resident = ok && !leader && b0 + ns >= nbatch && b0 < nbatch;
+    resident = ok && !leader && b0 < nbatch && nproc == 1;
     if (!ok && tid == 0) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
     return block_min_u64(best, tl.red64);
   };
@@ -333,28 +351,36 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       }
       if (tid == 0) tl.flag = wait_arrivals(tc, n_wait, ea.err, limit);
       __syncthreads();
-      bool stop = true;
+      bool stop = true, ok = false;
       int npx = 0, npy = 0;
+      unsigned long long t_b = 0ull;
       if (tl.flag) {
-        const unsigned long long t_b = globaltimer();
-        update_phase<R>(s, tpart, ns, usm);
-        __syncthreads();
-        stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
-        npx = __ldcg(&c->px);
-        npy = __ldcg(&c->py);
-        if (tid == 0) {
-          c->t_search += t_b - t_a;
-          c->t_update += globaltimer() - t_b;
-          c->timed_iters += 1;
+        t_b = globaltimer();
+        ok = update_phase<R>(s, tpart, ns, usm);  // ends with a __syncthreads
+        if (ok) {
+          // the next target is known: publish it before the bookkeeping
+          stop = usm.remaining <= 0 || usm.next_key == 0ull || usm.it + 1 >= __ldcg(&c->iter_limit) ||
+                 __ldcg(&c->status) != 0 || __ldcg(ea.err) != 0;
+          npx = usm.next_idx % s.W;
+          npy = usm.next_idx / s.W;
         }
       }
       __syncthreads();
       if (tid == 0) {
         tc->arrive = 0u;
+        tc->next = 0u;
         st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
         tl.stop = stop;
         tl.px = npx;
         tl.py = npy;
+      }
+      if (ok) {
+        update_finish<R>(s, usm);
+        if (tid == 0) {
+          c->t_search += t_b - t_a;
+          c->t_update += globaltimer() - t_b;
+          c->timed_iters += 1;
+        }
       }
       ++epoch;
       prev_px = px;
@@ -413,6 +439,7 @@ __global__ void __launch_bounds__(kEngThreads) k_update_fast(ImgState s, cudaGra
   spec_phase<R>(s, usm);
   __syncthreads();
   const bool ok = update_phase<R>(s, s.partial, s.n_partial, usm);
+  if (ok) update_finish<R>(s, usm);
   if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, ok && loop_active(s.ctrl) ? 1u : 0u);
 }
 

@@ -14,7 +14,8 @@ constexpr int kEngWarps = kEngThreads / 32;
 struct TeamCtl {
   unsigned long long pub;  // epoch | next px | next py | stop (release-published)
   unsigned arrive;         // searchers arrived in the current iteration
-  unsigned pad[29];        // keep teams on separate 128-byte lines
+  unsigned next;           // search batches handed out beyond the static first ones
+  unsigned pad[28];        // keep teams on separate 128-byte lines
 };
 
 struct EngineArgs {

@@ -83,11 +83,19 @@ __device__ inline uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
          ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
-__device__ inline void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// Same MMA with the descriptors given as 32-bit halves (the high halves of
+// every A and every B descriptor are the same constants), so a fully
+// unrolled issue loop only adds immediates to the low halves; ACC = 0
+// overwrites the accumulator.
+template <int ACC>
+__device__ inline void tc_mma_lo(uint32_t d, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi,
+                                 uint32_t idesc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+      "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+      "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "n"(ACC)
       : "memory");
 }
 
@@ -342,25 +350,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_search_tc(ImgState s, int nx,
         tc_fence_after();
         if (tile + (int)gridDim.x < ntiles) issue_tma(tile + gridDim.x);
         const uint32_t dcol = tmem + (uint32_t)((i & 1) * G::ACC);
-#pragma unroll 1
+        const uint32_t a_lo = (uint32_t)adesc0, a_hi = (uint32_t)(adesc0 >> 32);
+        const uint32_t b_lo = (uint32_t)bdesc0, b_hi = (uint32_t)(bdesc0 >> 32);
+        // descriptor units are 16 bytes; every offset below is a constant
+#pragma unroll
         for (int rho = 0; rho < G::NRHO; ++rho) {
-          const int par = rho & 1, t = rho >> 1;
 #pragma unroll
           for (int kc = 0; kc < G::KC; ++kc) {
-            const uint64_t ad = adesc0 + (uint64_t)(rho * (kTcPlaneW * 2 / 16) + 2 * kc);
-            const uint32_t first = (rho == 0 && kc == 0) ? 1u : 0u;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-              const uint64_t bd =
-                  bdesc0 + (uint64_t)((((ch * G::KC + kc) * 2 + par) * G::GB + G::TMAX - t) * 16);
-              tc_mma(dcol, ad + (uint64_t)(ch * (G::PLANE_BYTES / 16)), bd, idesc,
-                     (first && ch == 0) ? 0u : 1u);
+            const uint32_t ao = a_lo + (uint32_t)(rho * (kTcPlaneW * 2 / 16) + 2 * kc);
+            const int bstrip = (rho & 1) * G::GB + G::TMAX - (rho >> 1);  // + (kappa*KC+kc)*2*GB
+            if (rho == 0 && kc == 0) {
+              tc_mma_lo<0>(dcol, ao, a_hi, b_lo + (uint32_t)(((0 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
+              tc_mma_lo<0>(dcol + G::N, ao + 3 * (G::PLANE_BYTES / 16), a_hi,
+                           b_lo + (uint32_t)(((3 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
+              tc_mma_lo<0>(dcol + 2 * G::N, ao + 4 * (G::PLANE_BYTES / 16), a_hi,
+                           b_lo + (uint32_t)(((3 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
+            } else {
+              tc_mma_lo<1>(dcol, ao, a_hi, b_lo + (uint32_t)(((0 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
+              tc_mma_lo<1>(dcol + G::N, ao + 3 * (G::PLANE_BYTES / 16), a_hi,
+                           b_lo + (uint32_t)(((3 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
+              tc_mma_lo<1>(dcol + 2 * G::N, ao + 4 * (G::PLANE_BYTES / 16), a_hi,
+                           b_lo + (uint32_t)(((3 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
             }
-            const uint64_t bm =
-                bdesc0 + (uint64_t)((((3 * G::KC + kc) * 2 + par) * G::GB + G::TMAX - t) * 16);
-            tc_mma(dcol + G::N, ad + (uint64_t)(3 * (G::PLANE_BYTES / 16)), bm, idesc, first ? 0u : 1u);
-            tc_mma(dcol + 2 * G::N, ad + (uint64_t)(4 * (G::PLANE_BYTES / 16)), bm, idesc,
-                   first ? 0u : 1u);
+            tc_mma_lo<1>(dcol, ao + 1 * (G::PLANE_BYTES / 16), a_hi,
+                         b_lo + (uint32_t)(((1 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
+            tc_mma_lo<1>(dcol, ao + 2 * (G::PLANE_BYTES / 16), a_hi,
+                         b_lo + (uint32_t)(((2 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
           }
         }
         tc_commit(mma_bar + (i & 1));

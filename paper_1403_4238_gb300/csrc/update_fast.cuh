@@ -51,6 +51,13 @@ struct __align__(16) UpdSmem {
   int nlist;
   unsigned long long red64[32];
   int red32[32];
+  // outcome of update_phase, consumed by update_finish
+  unsigned long long next_key;  // priority key of the next target (0: none)
+  int next_idx;
+  int it, remaining, n_filled, n_known, n_cand, newly, qx, qy;
+  uint32_t ssd;
+  int px, py;
+  double pp, cp;
 };
 
 // Sobel normal of the Omega indicator at local (lx, ly) = image (x, y),
@@ -408,35 +415,77 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   }
   newly = block_sum_int(newly, sm.red32);
 
-  // tiles over the window, then the next target
+  // tiles over the window, then the next target (into shared memory; the
+  // control block is written by update_finish)
   block_refresh_tiles(s, max(0, px - R2), min(W - 1, px + R2), max(0, py - R2), min(H - 1, py + R2));
   remaining -= filled;
-  if (tid == 0) {
-    inpaint_step_info* e = &c->last;
-    e->iter = it;
-    e->px = px;
-    e->py = py;
-    e->qx = qx;
-    e->qy = qy;
-    e->ssd = ssd;
-    e->priority = pp;
-    e->confidence = cp;
-    e->filled = filled;
-    e->remaining = remaining;
-    e->n_known = n_known;
-    e->n_cand = n_cand;
-    if (it < s.trace_cap) s.trace[it] = *e;
-    c->remaining = remaining;
-    c->iter = it + 1;
-    c->n_valid = n_cand + newly;
-    c->evals += (unsigned long long)n_cand * (unsigned long long)n_known;
-    c->px = -1;
-    c->py = -1;
+  if (tid < 32) {
+    unsigned long long k = 0ull;
+    int idx = 0x7fffffff;
+    if (remaining > 0) warp_global_best(s, k, idx);
+    if (tid == 0) {
+      sm.next_key = k;
+      sm.next_idx = idx;
+      sm.it = it;
+      sm.remaining = remaining;
+      sm.n_filled = filled;
+      sm.n_known = n_known;
+      sm.n_cand = n_cand;
+      sm.newly = newly;
+      sm.qx = qx;
+      sm.qy = qy;
+      sm.ssd = ssd;
+      sm.px = px;
+      sm.py = py;
+      sm.pp = pp;
+      sm.cp = cp;
+    }
   }
   __syncthreads();
-  if (remaining > 0 && tid < 32) warp_select(s);
-  __syncthreads();
   return true;
+}
+
+// Records the iteration applied by update_phase (trace, counters) and
+// installs the next target p^ with its priority and confidence in the
+// control block.  Neither the image state nor the tiles change here, so the
+// persistent engine publishes the next target to its searchers first.
+// Whole block; ends with a __syncthreads.
+template <int R>
+__device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm) {
+  Ctrl* c = s.ctrl;
+  if (threadIdx.x == 0) {
+    inpaint_step_info* e = &c->last;
+    e->iter = sm.it;
+    e->px = sm.px;
+    e->py = sm.py;
+    e->qx = sm.qx;
+    e->qy = sm.qy;
+    e->ssd = sm.ssd;
+    e->priority = sm.pp;
+    e->confidence = sm.cp;
+    e->filled = sm.n_filled;
+    e->remaining = sm.remaining;
+    e->n_known = sm.n_known;
+    e->n_cand = sm.n_cand;
+    if (sm.it < s.trace_cap) s.trace[sm.it] = *e;
+    c->remaining = sm.remaining;
+    c->iter = sm.it + 1;
+    c->n_valid = sm.n_cand + sm.newly;
+    c->evals += (unsigned long long)sm.n_cand * (unsigned long long)sm.n_known;
+    c->px = -1;
+    c->py = -1;
+    if (sm.remaining > 0) {
+      if (sm.next_key == 0ull) {
+        c->status = INPAINT_ERR_INTERNAL;  // Omega non-empty but no front
+      } else {
+        c->px = sm.next_idx % s.W;
+        c->py = sm.next_idx / s.W;
+        c->prio = __longlong_as_double((long long)(sm.next_key - 1ull));
+        c->conf = __ldcg(&s.pconf[sm.next_idx]);
+      }
+    }
+  }
+  __syncthreads();
 }
 
 }  // namespace inp
