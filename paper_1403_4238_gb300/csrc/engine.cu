@@ -33,9 +33,9 @@ cudaError_t launch_prio_init_fast(const ImgState& s, cudaStream_t st) {
   return f ? f->prio_init(s, st) : cudaErrorInvalidValue;
 }
 
-// TMA descriptor of an image's RGBA words: 2-D (W, H), row pitch in bytes,
-// box box_w x box_h words; out-of-image reads give 0.
-int make_image_tmap_box(const ImgState& s, int box_w, int box_h, CUtensorMap* out) {
+// TMA descriptor of a 2-D array of 32-bit words (W x H, row pitch `pitch`
+// words), box box_w x box_h words; reads outside the array give 0.
+static int encode_2d(void* base, int W, int H, int pitch, int box_w, int box_h, CUtensorMap* out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -46,19 +46,26 @@ int make_image_tmap_box(const ImgState& s, int box_w, int box_h, CUtensorMap* ou
       return -1;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)s.W, (cuuint64_t)s.H};
-  const cuuint64_t strides[1] = {(cuuint64_t)s.pitch * 4};
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
   const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, s.img, dims, strides, box, estr,
+  const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-// The engine's search window: (128 + 2r rounded up to 4) x (16 * srw + 2r).
+int make_image_tmap_box(const ImgState& s, int box_w, int box_h, CUtensorMap* out) {
+  return encode_2d(s.img, s.W, s.H, s.pitch, box_w, box_h, out);
+}
+
+// The engine's two maps per image: out[0] the search window of RGBA words,
+// (128 + 2r rounded up to 4) x (16 * srw + 2r); out[1] the validity counts
+// of the batch's candidates, kEngCountW x (16 * srw) from a 4-word boundary.
 int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out) {
-  return make_image_tmap_box(s, (128 + 2 * s.r + 3) & ~3, kEngWarps * srw + 2 * s.r, out);
+  if (make_image_tmap_box(s, (128 + 2 * s.r + 3) & ~3, kEngWarps * srw + 2 * s.r, out) != 0) return -1;
+  return encode_2d(s.count, s.W, s.H, s.pitch, kEngCountW, kEngWarps * srw, out + 1);
 }
 
 }  // namespace inp

@@ -30,7 +30,10 @@ struct EngGeom {
   static constexpr int BW = (128 + 2 * R + 3) & ~3;  // staged width (words)
   static constexpr int B = kEngWarps * SRW;          // candidate rows per batch
   static constexpr int BH = B + 2 * R;               // staged rows
-  static constexpr int STAGE_BYTES = ((BW * BH * 4 + 127) / 128) * 128;
+  static constexpr int PIX_BYTES = ((BW * BH * 4 + 127) / 128) * 128;
+  static constexpr int CNT_BYTES = ((kEngCountW * B * 4 + 127) / 128) * 128;
+  static constexpr int STAGE_BYTES = PIX_BYTES + CNT_BYTES;  // pixel tile | count tile
+  static constexpr int COFF = R & 3;  // first candidate column within the count tile
   static constexpr int NROW = (4 + P - 1 + 3) & ~3;  // strip words per lane
   static constexpr int TP = (P + 3) & ~3;            // padded target row (words)
   static constexpr unsigned FULL = (1u << P) - 1u;
@@ -121,12 +124,25 @@ struct EngSmemTail {
 constexpr int kTgtWords = 17 * 20 + 17 + 3;  // padded target rows + row masks (R <= 8)
 constexpr size_t kHeadBytes = ((((sizeof(EngSmemTail) + 15) & ~size_t(15)) + kTgtWords * 4 + 127) / 128) * 128;
 
+// Shared memory of an engine CTA: head | two search stages | update state |
+// update cache (the leader keeps its speculative state while it searches).
+template <int R>
+__host__ __device__ constexpr size_t upd_smem_bytes() {
+  return ((sizeof(UpdSmem<R>) + 127) / 128) * 128 + sizeof(UpdCache<R>);
+}
+
 template <int R, int SRW>
 __host__ __device__ constexpr size_t eng_smem_bytes() {
   using G = EngGeom<R, SRW>;
-  const size_t srch = (size_t)2 * G::STAGE_BYTES;
-  const size_t upd = sizeof(UpdSmem<R>);
-  return kHeadBytes + (srch > upd ? srch : upd) + 128;
+  return kHeadBytes + (size_t)2 * G::STAGE_BYTES + upd_smem_bytes<R>() + 128;
+}
+
+static_assert(eng_smem_bytes<8, 2>() <= 227 * 1024, "engine CTA must fit in shared memory");
+static_assert(eng_smem_bytes<7, 2>() <= 227 * 1024, "engine CTA must fit in shared memory");
+
+template <int R>
+__device__ inline UpdCache<R>& upd_cache_of(uint8_t* upd_base) {
+  return *reinterpret_cast<UpdCache<R>*>(upd_base + ((sizeof(UpdSmem<R>) + 127) / 128) * 128);
 }
 
 // Team publication word: epoch (bits 0-31), next target px (32-46), py
@@ -206,7 +222,8 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   uint8_t* big = smem + kHeadBytes;
   uint32_t* stage0 = reinterpret_cast<uint32_t*>(big);
   uint32_t* stage1 = reinterpret_cast<uint32_t*>(big + G::STAGE_BYTES);
-  UpdSmem<R>& usm = *reinterpret_cast<UpdSmem<R>*>(big);
+  UpdSmem<R>& usm = *reinterpret_cast<UpdSmem<R>*>(big + 2 * G::STAGE_BYTES);
+  UpdCache<R>& uca = upd_cache_of<R>(big + 2 * G::STAGE_BYTES);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rank = x.rank, tsize = x.tsize;
   TeamCtl* tc = x.tc;
@@ -216,7 +233,8 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   unsigned epoch = x.epoch;
 
   const ImgState s = ea.imgs[j];
-  const CUtensorMap* map = &ea.tmaps[j];
+  const CUtensorMap* map = &ea.tmaps[2 * j];
+  const CUtensorMap* cmap = &ea.tmaps[2 * j + 1];
   Ctrl* c = s.ctrl;
   const int xb = R + ((s.cx0 - R) & ~3);
   const int ncg = s.cx1 >= s.cx0 ? (s.cx1 - xb + 128) / 128 : 0;
@@ -245,6 +263,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   }
   __syncthreads();
   int prev_px = -1000000, prev_py = -1000000;
+  bool staged = false;  // leader: neighbourhood of the next p^ already in shared memory
 
   // One search round for target (px, py): this CTA's batches; returns its
   // best key.  Whole block.
@@ -255,15 +274,19 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     const bool need0 = !resident ||
                        (abs(prev_px - (xb + 128 * (b0 % max(ncg, 1)) + 64)) <= 64 + 2 * R + 4 &&
                         abs(prev_py - (s.cy0 + B * (b0 / max(ncg, 1)) + B / 2)) <= B / 2 + 2 * R + 1);
-    auto issue = [&](int b, uint32_t* st, uint64_t* bar) {
+    // a batch's stage: its RGBA window (unless still resident) and the
+    // validity counts of its candidates, on one mbarrier
+    auto issue = [&](int b, uint32_t* st, uint64_t* bar, bool pixels) {
       const int gx = b % ncg, gy = b / ncg;
       asm volatile("fence.proxy.async;" ::: "memory");
-      mbar_expect_tx(bar, (uint32_t)(G::BW * G::BH * 4));
-      tma_load_2d(st, map, xb - R + 128 * gx, s.cy0 + B * gy - R, bar);
+      mbar_expect_tx(bar, (uint32_t)((pixels ? G::BW * G::BH * 4 : 0) + kEngCountW * B * 4));
+      if (pixels) tma_load_2d(st, map, xb - R + 128 * gx, s.cy0 + B * gy - R, bar);
+      tma_load_2d(reinterpret_cast<uint8_t*>(st) + G::PIX_BYTES, cmap, xb - G::COFF + 128 * gx,
+                  s.cy0 + B * gy, bar);
     };
     if (tid == 0) {
       tl.bcur = b0 < nbatch ? b0 : (nbatch > nst ? grab() : nbatch);
-      if (tl.bcur < nbatch && (tl.bcur != b0 || need0)) issue(tl.bcur, stage0, &tl.full[0]);
+      if (tl.bcur < nbatch) issue(tl.bcur, stage0, &tl.full[0], tl.bcur != b0 || need0);
     }
     // target patch: one thread per pixel, then the row masks
     if (tid < P * P) {
@@ -292,34 +315,28 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       if (tid == 0) {
         const int nb = nbatch > nst ? grab() : nbatch;
         tl.bnx[cur] = nb;  // read by all after the barrier at the end of this batch
-        if (nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1]);
+        if (nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1], true);
       }
       const int gx = b % ncg, gy = b / ncg;
       const int qx0 = xb + 128 * gx + lane * 4, qy0 = s.cy0 + B * gy + warp * SRW;
-      int cnt[SRW][4];
+      const bool got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
+      if (cur) ph1 ^= 1; else ph0 ^= 1;
+      const uint32_t* stg = cur ? stage1 : stage0;
+      uint32_t acc[SRW][4];
+      compute_rows<R, SRW>(stg, warp * SRW, tgt, rowmask, acc);
+      const int* cst = reinterpret_cast<const int*>(reinterpret_cast<const uint8_t*>(stg) + G::PIX_BYTES);
 #pragma unroll
       for (int o = 0; o < SRW; ++o)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int qx = qx0 + k, qy = qy0 + o;
-          cnt[o][k] = (qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1) ? __ldcg(&s.count[(size_t)qy * s.W + qx]) : 1;
-        }
-      bool got = true;
-      if (b != b0 || need0) {
-        got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
-        if (cur) ph1 ^= 1; else ph0 ^= 1;
-      }
-      uint32_t acc[SRW][4];
-      compute_rows<R, SRW>(cur ? stage1 : stage0, warp * SRW, tgt, rowmask, acc);
-#pragma unroll
-      for (int o = 0; o < SRW; ++o)
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (cnt[o][k] == 0) {
-            const unsigned idx = (unsigned)((qy0 + o) * s.W + qx0 + k);
+          const bool in = qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1;
+          if (in && cst[(warp * SRW + o) * kEngCountW + G::COFF + lane * 4 + k] == 0) {
+            const unsigned idx = (unsigned)(qy * s.W + qx);
             const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
             best = key < best ? key : best;
           }
+        }
       ++nproc;
       if (__syncthreads_or(!got)) {  // a bounded wait gave up: stop uniformly
         ok = false;
@@ -343,8 +360,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     const int px = tl.px, py = tl.py;
     if (leader) {
       const unsigned long long t_a = globaltimer();
-      spec_phase<R>(s, usm);
-      __syncthreads();
+      spec_phase<R>(s, usm, uca, staged);
       if (searcher) {
         const unsigned long long best = search_round(px, py);
         if (tid == 0) tpart[rank] = best;
@@ -356,7 +372,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       unsigned long long t_b = 0ull;
       if (tl.flag) {
         t_b = globaltimer();
-        ok = update_phase<R>(s, tpart, ns, usm);  // ends with a __syncthreads
+        ok = update_phase<R>(s, tpart, ns, usm, uca);  // ends with a __syncthreads
         if (ok) {
           // the next target is known: publish it before the bookkeeping
           stop = usm.remaining <= 0 || usm.next_key == 0ull || usm.it + 1 >= __ldcg(&c->iter_limit) ||
@@ -374,6 +390,8 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
         tl.px = npx;
         tl.py = npy;
       }
+      staged = ok && !stop;
+      if (staged) stage_nbhd<R, true, true>(s, npx, npy, usm);  // next speculative phase's input
       if (ok) {
         update_finish<R>(s, usm);
         if (tid == 0) {
@@ -430,22 +448,22 @@ namespace inp {
 template <int R>
 __global__ void __launch_bounds__(kEngThreads) k_update_fast(ImgState s, cudaGraphConditionalHandle cond,
                                                             int use_cond) {
-  extern __shared__ __align__(16) uint8_t sm_raw[];
+  extern __shared__ __align__(128) uint8_t sm_raw[];
   UpdSmem<R>& usm = *reinterpret_cast<UpdSmem<R>*>(sm_raw);
+  UpdCache<R>& uca = upd_cache_of<R>(sm_raw);
   if (!loop_active(s.ctrl)) {
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
     return;
   }
-  spec_phase<R>(s, usm);
-  __syncthreads();
-  const bool ok = update_phase<R>(s, s.partial, s.n_partial, usm);
+  spec_phase<R>(s, usm, uca, false);
+  const bool ok = update_phase<R>(s, s.partial, s.n_partial, usm, uca);
   if (ok) update_finish<R>(s, usm);
   if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, ok && loop_active(s.ctrl) ? 1u : 0u);
 }
 
 template <int R>
 static cudaError_t upd_fast_t(const ImgState& s, unsigned long long cond, int use_cond, cudaStream_t st) {
-  const size_t smem = sizeof(UpdSmem<R>);
+  const size_t smem = upd_smem_bytes<R>();
   cudaError_t e = cudaFuncSetAttribute(k_update_fast<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -245,13 +245,13 @@ int setup_engine(inpaint_ctx* c) {
   c->eng_grid = g2 < grid ? g2 : grid;
   c->eng_sr = sr;
   c->st.srw = sr;
-  if (!alloc_n(c, c->d_img, 1) || !alloc_n(c, c->d_tmap, 1) ||
+  if (!alloc_n(c, c->d_img, 1) || !alloc_n(c, c->d_tmap, 2) ||
       !alloc_n(c, c->d_ints, (size_t)c->eng_grid + 5) || !alloc_n(c, c->d_team, 1) ||
       !alloc_n(c, c->d_epart, (size_t)c->eng_grid) || !alloc_n(c, c->d_err, 1))
     return INPAINT_ERR_NOMEM;
   if (!c->h_err && cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) return INPAINT_ERR_NOMEM;
-  CUtensorMap tm;
-  if (make_image_tmap(c->st, sr, &tm) != 0) {
+  CUtensorMap tm[2];
+  if (make_image_tmap(c->st, sr, tm) != 0) {
     g_last_error = "cuTensorMapEncodeTiled failed";
     return INPAINT_ERR_CUDA;
   }
@@ -262,7 +262,7 @@ int setup_engine(inpaint_ctx* c) {
   ints[c->eng_grid + 3] = 1;            // team_img_off = {0, 1}
   ints[c->eng_grid + 4] = 0;            // team_img = {0}
   CK(cudaMemcpyAsync(c->d_img, &c->st, sizeof(ImgState), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->d_tmap, &tm, sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_tmap, tm, 2 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice,
                      c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -403,13 +403,13 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
   }
   const size_t n = (size_t)W * H;
   if (!alloc_n(c, s.img, (size_t)s.pitch * H) || !alloc_n(c, s.omega, n) || !alloc_n(c, s.gray, n) ||
-      !alloc_n(c, s.conf, n) || !alloc_n(c, s.count, n) || !alloc_n(c, s.prio, n) ||
+      !alloc_n(c, s.conf, n) || !alloc_n(c, s.count, (size_t)s.pitch * H) || !alloc_n(c, s.prio, n) ||
       !alloc_n(c, s.pconf, n) || !alloc_n(c, s.tiles0, (size_t)s.t0x * s.t0y) ||
       !alloc_n(c, s.tiles1, (size_t)s.t1x * s.t1y) ||
       !alloc_n(c, s.ctrl, 1) || !alloc_n(c, s.trace, (size_t)s.trace_cap) ||
       !alloc_n(c, s.partial, (size_t)(s.n_partial > 0 ? s.n_partial : 1)) ||
       !alloc_n(c, c->sat, (size_t)(W + 1) * (H + 1) + (size_t)sat_chunks(H) * W) || !alloc_n(c, c->rgb_stage, 3 * n) ||
-      !alloc_n(c, c->mask_stage, n) || !alloc_n(c, s.spec, 1)) {
+      !alloc_n(c, c->mask_stage, n)) {
     g_last_error = "device allocation failed";
     return fail(INPAINT_ERR_NOMEM);
   }
@@ -852,7 +852,7 @@ int engine_set_prepare(EngineSet& es, const std::vector<inpaint_ctx*>& cs, const
   es.n_teams = (int)es.team_size.size();
   const int G = es.grid, T = es.n_teams;
   std::vector<ImgState> imgs(n);
-  std::vector<CUtensorMap> maps(n);
+  std::vector<CUtensorMap> maps(2 * (size_t)n);
   es.smem = 0;
   for (int i = 0; i < n; ++i) {
     inpaint_ctx* c = cs[i];
@@ -861,7 +861,7 @@ int engine_set_prepare(EngineSet& es, const std::vector<inpaint_ctx*>& cs, const
     if (!sr) sr = pick_rows_per_warp(c->st, es.team_size[es.img_team[i]]);
     c->st.srw = sr;
     imgs[i] = c->st;
-    if (make_image_tmap(c->st, sr, &maps[i]) != 0) {
+    if (make_image_tmap(c->st, sr, &maps[2 * (size_t)i]) != 0) {
       g_last_error = "cuTensorMapEncodeTiled failed";
       return INPAINT_ERR_CUDA;
     }
@@ -883,7 +883,7 @@ int engine_set_prepare(EngineSet& es, const std::vector<inpaint_ctx*>& cs, const
   ints.insert(ints.end(), lst.begin(), lst.end());
   // one device block: states | maps | teams | partials | ints | err
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t b_imgs = up(sizeof(ImgState) * n), b_maps = up(sizeof(CUtensorMap) * n);
+  const size_t b_imgs = up(sizeof(ImgState) * n), b_maps = up(sizeof(CUtensorMap) * 2 * n);
   const size_t b_teams = up(sizeof(TeamCtl) * T), b_part = up(sizeof(unsigned long long) * G);
   const size_t b_ints = up(sizeof(int) * ints.size()), b_err = 256;
   const size_t need = b_imgs + b_maps + b_teams + b_part + b_ints + b_err;
@@ -912,7 +912,7 @@ int engine_set_prepare(EngineSet& es, const std::vector<inpaint_ctx*>& cs, const
   int* d_ints = (int*)(base + b_imgs + b_maps + b_teams + b_part);
   es.d_err = (int*)(base + b_imgs + b_maps + b_teams + b_part + b_ints);
   CK(cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(ImgState) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_maps, maps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_maps, maps.data(), sizeof(CUtensorMap) * 2 * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
   EngineArgs& ea = es.ea;

@@ -9,6 +9,7 @@ namespace inp {
 
 constexpr int kEngThreads = 512;
 constexpr int kEngWarps = kEngThreads / 32;
+constexpr int kEngCountW = 132;  // count words staged per batch row (128 + alignment)
 
 // Per-team synchronisation words (global memory).
 struct TeamCtl {
@@ -20,7 +21,7 @@ struct TeamCtl {
 
 struct EngineArgs {
   const ImgState* imgs;        // [n_imgs]
-  const CUtensorMap* tmaps;    // [n_imgs], 64-byte aligned
+  const CUtensorMap* tmaps;    // [2 * n_imgs]: pixels, counts per image; 64-byte aligned
   const int* cta_team;         // [grid]
   const int* team_first;       // [n_teams + 1] first CTA of each team
   const int* team_img_off;     // [n_teams + 1] offsets into team_img
@@ -77,7 +78,7 @@ const EngineFns* engine_fns(int r);
 // engine_fns(r)->smem_bytes(srw) over the images of the launch.
 cudaError_t engine_occupancy(size_t smem, int* blocks_per_sm);
 cudaError_t engine_launch(size_t smem, const EngineArgs& ea, int grid, cudaStream_t st);
-int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out);
+int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out);  // writes out[0], out[1]
 int make_image_tmap_box(const ImgState& s, int box_w, int box_h, CUtensorMap* out);
 cudaError_t launch_update_fast(const ImgState& s, unsigned long long cond, int use_cond,
                                cudaStream_t st);

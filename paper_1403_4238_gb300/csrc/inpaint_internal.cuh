@@ -8,8 +8,10 @@
 //   omega  uint8[W*H]    1 = pixel of the target region Omega (still unknown)
 //   gray   uint8[W*H]    integer luma of known pixels (0 under Omega)
 //   conf   double[W*H]   confidence C (Eq. 2), 0 under Omega
-//   count  int32[W*H]    for a candidate centre q: unknown pixels in Psi_q
-//                        (valid source patch iff 0); borders hold a large value
+//   count  int32[H*pitch] for a candidate centre q: unknown pixels in Psi_q
+//                        (valid source patch iff 0); borders and the row
+//                        padding hold a large value; same pitch as img so a
+//                        TMA tile of counts can ride with the pixel tile
 //   prio   uint64[W*H]   priority key of a front pixel: bits(P(p)) + 1; 0 off
 //                        the front (P >= 0, so the bits order like the values)
 //   pconf  double[W*H]   C(p) of the last priority evaluation at p
@@ -71,20 +73,11 @@ struct Ctrl {
   int pad1;
 };
 
-// Output of the speculative phase of an iteration (see update_fast.cuh): for
-// each pixel of the (4R+3)^2 window around p^, the post-fill confidence term
-// and front normal.  Sized for R <= 8.
-constexpr int kSpecMax = 35 * 35;
+// Window codes of the speculative phase (update_fast.cuh): a pixel of the
+// (4R+3)^2 priority window is outside the image, or in the image and not on
+// the post-fill front; front pixels carry their packed normal instead.
 constexpr int kSpecOutside = -2;   // window pixel outside the image
 constexpr int kSpecNotFront = -1;  // in the image, not on the post-fill front
-struct SpecBuf {
-  double C[kSpecMax];
-  int nrm[kSpecMax];
-  uint16_t front[kSpecMax];  // window indices of the post-fill front pixels
-  int nfront;
-  int iter;    // iteration described
-  int filled;  // pixels that iteration fills
-};
 
 // Thread that handles entry k of a compact work list: consecutive entries go
 // to warps 0..3 in turn (one warp per SM sub-partition), so a short list of
@@ -129,7 +122,7 @@ struct ImgState {
   uint8_t* omega;
   uint8_t* gray;
   double* conf;
-  int32_t* count;
+  int32_t* count;          // unknown pixels of Psi_q per centre, row pitch `pitch`
   unsigned long long* prio;
   double* pconf;
   PrioBest* tiles0;
@@ -137,7 +130,6 @@ struct ImgState {
   Ctrl* ctrl;
   inpaint_step_info* trace;
   unsigned long long* partial;  // per-CTA best search key of the iteration
-  SpecBuf* spec;                // speculative-phase output (R <= 8)
   const double* dtab;           // data-term table (device, shared by contexts)
 };
 

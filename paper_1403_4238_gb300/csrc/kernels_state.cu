@@ -232,8 +232,10 @@ __global__ void k_count(ImgState s, const int32_t* sat) {
       const size_t a = (size_t)(y - r) * W1, b = (size_t)(y + r + 1) * W1;
       cnt = sat[b + x + r + 1] - sat[a + x + r + 1] - sat[b + x - r] + sat[a + x - r];
     }
-    s.count[(size_t)y * s.W + x] = cnt;
+    s.count[(size_t)y * s.pitch + x] = cnt;
     valid = (cnt == 0 && in_rect(s, x, y)) ? 1 : 0;
+  } else if (x < s.pitch) {
+    s.count[(size_t)y * s.pitch + x] = kCountInvalid;  // row padding
   }
   const int tot = block_sum_int(valid, scratch);
   if (threadIdx.x == 0 && tot) atomicAdd(&s.ctrl->n_valid, tot);
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(ImgState s, int do_fill,
       const int dec = sm.fsat[(v1 + 1) * P1 + u1 + 1] - sm.fsat[v0 * P1 + u1 + 1] -
                       sm.fsat[(v1 + 1) * P1 + u0] + sm.fsat[v0 * P1 + u0];
       if (dec) {
-        const size_t qi = (size_t)y * W + x;
+        const size_t qi = (size_t)y * s.pitch + x;
         const int nv = s.count[qi] - dec;
         s.count[qi] = nv;
         if (nv == 0 && in_rect(s, x, y)) ++newly;
@@ -430,15 +432,15 @@ __global__ void k_verify(ImgState s) {
   const int y = blockIdx.y;
   if (x >= s.W || s.ctrl->status != 0) return;
   const int r = s.r;
-  const size_t i = (size_t)y * s.W + x;
+  const size_t i = (size_t)y * s.W + x, ic = (size_t)y * s.pitch + x;
   bool bad = false;
   if (x - r >= 0 && x + r < s.W && y - r >= 0 && y + r < s.H) {
     int cnt = 0;
     for (int dy = -r; dy <= r; ++dy)
       for (int dx = -r; dx <= r; ++dx) cnt += s.omega[(size_t)(y + dy) * s.W + x + dx];
-    bad |= cnt != s.count[i];
+    bad |= cnt != s.count[ic];
   } else {
-    bad |= s.count[i] < kCountInvalid - (2 * r + 1) * (2 * r + 1);
+    bad |= s.count[ic] < kCountInvalid - (2 * r + 1) * (2 * r + 1);
   }
   unsigned long long key = 0ull;
   if (on_front(s, x, y)) {
@@ -471,7 +473,7 @@ static cudaError_t init_tail(const ImgState& s, int32_t* sat, cudaStream_t st) {
   k_sat_chunk_prefix<<<(W + 127) / 128, 128, 0, st>>>(s, tot, nch);
   if (H > kSatChunk) k_sat_cols_apply<<<dim3((W + 127) / 128, H - kSatChunk), 128, 0, st>>>(s, sat, tot);
   const dim3 rows((W + 255) / 256, H);
-  k_count<<<rows, 256, 0, st>>>(s, sat);
+  k_count<<<dim3((s.pitch + 255) / 256, H), 256, 0, st>>>(s, sat);
   if (s.r <= 8) {
     const cudaError_t e = launch_prio_init_fast(s, st);
     if (e != cudaSuccess) return e;

@@ -24,7 +24,7 @@ namespace inp {
 __device__ inline unsigned long long cand_key(const ImgState& s, uint32_t ssd, int qx, int qy) {
   if (qx > s.cx1 || qy > s.cy1) return ~0ull;
   const int idx = qy * s.W + qx;
-  if (s.count[idx] != 0) return ~0ull;
+  if (s.count[(size_t)qy * s.pitch + qx] != 0) return ~0ull;
   return ((unsigned long long)ssd << 32) | (unsigned)idx;
 }
 

@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_search_tc(ImgState s, int nx,
         for (int b = 0; b < 8; ++b) {
           const int u = 8 * a_blk + b, qx = t.x0 + u + R;
           cnt[kk][b] = (k < G::RP && qy <= s.cy1 && u < G::TS && qx >= s.cx0 && qx <= s.cx1)
-                           ? __ldcg(&s.count[(size_t)qy * s.W + qx])
+                           ? __ldcg(&s.count[(size_t)qy * s.pitch + qx])
                            : 1;
         }
       }

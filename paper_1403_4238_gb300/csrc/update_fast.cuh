@@ -33,6 +33,28 @@ struct UpdGeom {
   static constexpr int R2 = 2 * R + 1;  // priorities that can change
   static constexpr int NW = 2 * R2 + 1;
   static constexpr int NC = 4 * R + 1;  // validity counts that can change
+  // level-0 / level-1 priority tiles an NW x NW window can touch (per axis)
+  static constexpr int KT0 = (NW + kT0 - 2) / kT0 + 1;
+  static constexpr int KT1 = 2;
+};
+
+constexpr int kT1Cache = 512;  // level-1 entries kept in shared memory (images up to 2^25 px)
+
+// State the update phase reads that the search does not change, loaded
+// while the search runs (update_prefetch): validity counts of the count
+// window, the priority keys of the level-0 tiles the priority window
+// touches, the level-0 entries of the level-1 tiles over them, and the
+// level-1 entries of the whole image.
+template <int R>
+struct __align__(16) UpdCache {
+  using G = UpdGeom<R>;
+  unsigned long long tp[G::KT0 * G::KT0 * kT0 * kT0];
+  PrioBest t0c[G::KT1 * G::KT1 * kT1 * kT1];
+  PrioBest t1c[kT1Cache];
+  int cnt[G::NC * G::NC];
+  int tx0, ty0, ntx, nty;  // level-0 tiles [tx0, tx0 + ntx) x [ty0, ty0 + nty)
+  int ux0, uy0, nux, nuy;  // level-1 tiles
+  int t1n;                 // level-1 entries cached (0: read them from global memory)
 };
 
 template <int R>
@@ -51,6 +73,7 @@ struct __align__(16) UpdSmem {
   int nlist;
   unsigned long long red64[32];
   int red32[32];
+  int spec_iter, spec_filled, nfront;  // speculative phase outcome
   // outcome of update_phase, consumed by update_finish
   unsigned long long next_key;  // priority key of the next target (0: none)
   int next_idx;
@@ -224,28 +247,118 @@ __global__ void __launch_bounds__(256, 2) k_prio_init_fast(ImgState s) {
   }
 }
 
-// Speculative phase: post-fill front, normals and confidence terms of the
-// window around p^, written to s.spec.  Whole block.
+// Loads what the update phase of target (px, py) reads but the search does
+// not change (see UpdCache), with threads [first, blockDim.x).  No barrier.
 template <int R>
-__device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm) {
+__device__ void update_prefetch(const ImgState& s, UpdCache<R>& ca, int first) {
+  using G = UpdGeom<R>;
+  constexpr int R2 = G::R2, NC = G::NC;
+  const Ctrl* c = s.ctrl;
+  const int px = __ldcg(&c->px), py = __ldcg(&c->py);
+  const int W = s.W, H = s.H;
+  const int tx0 = max(0, px - R2) / kT0, tx1 = min(W - 1, px + R2) / kT0;
+  const int ty0 = max(0, py - R2) / kT0, ty1 = min(H - 1, py + R2) / kT0;
+  const int ntx = tx1 - tx0 + 1, nty = ty1 - ty0 + 1;
+  const int ux0 = tx0 / kT1, ux1 = tx1 / kT1, uy0 = ty0 / kT1, uy1 = ty1 / kT1;
+  const int nux = ux1 - ux0 + 1, nuy = uy1 - uy0 + 1;
+  const int n1 = s.t1x * s.t1y;
+  if ((int)threadIdx.x < first) return;
+  for (int j = threadIdx.x - first; j < NC * NC; j += blockDim.x - first) {
+    const int x = px + j % NC - 2 * R, y = py + j / NC - 2 * R;
+    ca.cnt[j] = (x >= 0 && x < W && y >= 0 && y < H) ? __ldcg(&s.count[(size_t)y * s.pitch + x]) : 0;
+  }
+  for (int e = threadIdx.x - first; e < ntx * nty * kT0 * kT0; e += blockDim.x - first) {
+    const int t = e / (kT0 * kT0), j = e % (kT0 * kT0);
+    const int x = (tx0 + t % ntx) * kT0 + (j & (kT0 - 1)), y = (ty0 + t / ntx) * kT0 + j / kT0;
+    ca.tp[e] = (x < W && y < H) ? __ldcg(&s.prio[(size_t)y * W + x]) : 0ull;
+  }
+  for (int e = threadIdx.x - first; e < nux * nuy * kT1 * kT1; e += blockDim.x - first) {
+    const int u = e / (kT1 * kT1), j = e % (kT1 * kT1);
+    const int tx = (ux0 + u % nux) * kT1 + (j & (kT1 - 1)), ty = (uy0 + u / nux) * kT1 + j / kT1;
+    PrioBest b;
+    b.key = 0ull;
+    b.idx = 0x7fffffff;
+    b.pad = 0;
+    if (tx < s.t0x && ty < s.t0y) {
+      b.key = __ldcg(&s.tiles0[ty * s.t0x + tx].key);
+      b.idx = __ldcg(&s.tiles0[ty * s.t0x + tx].idx);
+    }
+    ca.t0c[e] = b;
+  }
+  if (n1 <= kT1Cache)
+    for (int e = threadIdx.x - first; e < n1; e += blockDim.x - first) {
+      PrioBest b;
+      b.key = __ldcg(&s.tiles1[e].key);
+      b.idx = __ldcg(&s.tiles1[e].idx);
+      b.pad = 0;
+      ca.t1c[e] = b;
+    }
+  if ((int)threadIdx.x == first) {
+    ca.tx0 = tx0;
+    ca.ty0 = ty0;
+    ca.ntx = ntx;
+    ca.nty = nty;
+    ca.ux0 = ux0;
+    ca.uy0 = uy0;
+    ca.nux = nux;
+    ca.nuy = nuy;
+    ca.t1n = n1 <= kT1Cache ? n1 : 0;
+  }
+}
+
+// Integral image of the filled flags of Psi_p^ (validity-count
+// decrements); one warp.
+template <int R>
+__device__ inline void warp_fsat(UpdSmem<R>& sm) {
+  constexpr int P = UpdGeom<R>::P, P1 = P + 1;
+  const int lane = threadIdx.x & 31;
+  for (int v = lane; v <= P; v += 32) {
+    sm.fsat[v] = 0;
+    sm.fsat[v * P1] = 0;
+  }
+  __syncwarp();
+  for (int v = lane; v < P; v += 32) {
+    int run = 0;
+    for (int u = 0; u < P; ++u) {
+      run += sm.filled[v * P + u];
+      sm.fsat[(v + 1) * P1 + u + 1] = run;
+    }
+  }
+  __syncwarp();
+  for (int u = lane + 1; u <= P; u += 32)
+    for (int v = 2; v <= P; ++v) sm.fsat[v * P1 + u] += sm.fsat[(v - 1) * P1 + u];
+}
+
+// Speculative phase: post-fill mask, grey levels and confidences of the
+// neighbourhood of p^, the filled set and its integral image, the post-fill
+// front of the window with its normals and confidence terms.  Everything
+// stays in shared memory for update_phase.  Whole block.
+// `staged`: the neighbourhood of p^ is already in shared memory (the engine
+// stages it while it records the previous iteration).
+template <int R>
+__device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, bool staged) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW;
   const Ctrl* c = s.ctrl;
   const int px = __ldcg(&c->px), py = __ldcg(&c->py), it = __ldcg(&c->iter);
   const double cp = __ldcg(&c->conf);
-  stage_nbhd<R, false, true>(s, px, py, sm);
-  __syncthreads();
+  if (!staged) {
+    stage_nbhd<R, true, true>(s, px, py, sm);
+    __syncthreads();
+  }
   int my = 0;
   for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
     const int l = (RB + i / P - R) * NS + RB + i % P - R;
+    uint8_t f = 0;
     if (sm.om[l] == 1) {
       sm.om[l] = 0;
       sm.cf[l] = cp;
+      f = 1;
       ++my;
     }
+    sm.filled[i] = f;
   }
   const int filled = block_sum_int(my, sm.red32);  // includes __syncthreads
-  SpecBuf* sp = s.spec;
   // post-fill front of the window, compacted
   if (threadIdx.x == 0) sm.nlist = 0;
   __syncthreads();
@@ -256,34 +369,43 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm) {
       nrm = kSpecNotFront;
       if (front_local(sm.om, l, NS)) sm.list[atomicAdd(&sm.nlist, 1)] = (uint16_t)i;
     }
-    sp->nrm[i] = nrm;  // front entries are overwritten below
+    sm.snrm[i] = nrm;  // front entries are overwritten below
   }
   __syncthreads();
   const int nfront = sm.nlist;
-  // one long FP64 chain per front pixel, spread over the four sub-partitions
-  for (int t = threadIdx.x; t < ((nfront + 127) & ~127); t += blockDim.x) {
+  // one long FP64 chain per front pixel, spread over the four sub-partitions;
+  // the warps the chains leave idle build the filled-flag integral image and
+  // load the update phase's cache meanwhile
+  const int nchain = (nfront + 127) & ~127;  // threads [0, nchain) run chains
+  for (int t = threadIdx.x; t < nchain; t += blockDim.x) {
     const int k = list_entry(t);
     if (k >= nfront) continue;
     const int i = sm.list[k];
     const int wx = i % NW - R2, wy = i / NW - R2;
     const int lx = RB + wx, ly = RB + wy, x = px + wx, y = py + wy;
-    sp->C[i] = conf_local<R>(sm, s, lx, ly, x, y);
-    sp->nrm[i] = normal_local<R>(sm, s, lx, ly, x, y);
-    sp->front[k] = (uint16_t)i;
+    sm.sC[i] = conf_local<R>(sm, s, lx, ly, x, y);
+    sm.snrm[i] = normal_local<R>(sm, s, lx, ly, x, y);
   }
+  const int nt = (int)blockDim.x;
+  const bool spare = nchain + 64 <= nt;  // at least two warps without chains
+  const int fsat_warp = spare ? nchain / 32 : 0;
+  if ((int)(threadIdx.x >> 5) == fsat_warp) warp_fsat<R>(sm);
+  update_prefetch<R>(s, ca, spare ? nchain + 32 : 0);
   if (threadIdx.x == 0) {
-    sp->nfront = nfront;
-    sp->iter = it;
-    sp->filled = filled;
+    sm.nfront = nfront;
+    sm.spec_iter = it;
+    sm.spec_filled = filled;
   }
+  __syncthreads();
 }
 
 // Update phase: applies the iteration whose best source key is the minimum
-// of partial[0..n_partial).  Returns false (status written) when there is no
-// source patch or the state is inconsistent.  Whole block.
+// of partial[0..n_partial), on the state prepared by spec_phase and
+// update_prefetch.  Returns false (status written) when there is no source
+// patch or the state is inconsistent.  Whole block; ends with a __syncthreads.
 template <int R>
 __device__ bool update_phase(const ImgState& s, const unsigned long long* partial, int n_partial,
-                             UpdSmem<R>& sm) {
+                             UpdSmem<R>& sm, UpdCache<R>& ca) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW, NC = G::NC;
   Ctrl* c = s.ctrl;
@@ -293,25 +415,23 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const double cp = __ldcg(&c->conf), pp = __ldcg(&c->prio);
   const int n_cand = __ldcg(&c->n_valid), it = __ldcg(&c->iter);
   int remaining = __ldcg(&c->remaining);
-  const SpecBuf* sp = s.spec;
 
-  // best source key, staged mask + grey, speculative window terms
+  // best source key
   unsigned long long best = ~0ull;
   for (int i = tid; i < n_partial; i += nt) {
     const unsigned long long v = __ldcg(&partial[i]);
     best = v < best ? v : best;
   }
-  stage_nbhd<R, true, false>(s, px, py, sm);
-  for (int i = tid; i < NW * NW; i += nt) {
-    sm.sC[i] = __ldcg(&sp->C[i]);
-    sm.snrm[i] = __ldcg(&sp->nrm[i]);
-    sm.list[i] = __ldcg(&sp->front[i]);
-  }
-  const int spec_iter = __ldcg(&sp->iter), spec_filled = __ldcg(&sp->filled);
-  const int nfront = __ldcg(&sp->nfront);
   best = block_min_u64(best, sm.red64);
   if (best == ~0ull) {
     if (tid == 0) c->status = INPAINT_ERR_NO_SOURCE;
+    __syncthreads();
+    return false;
+  }
+  const int filled = sm.spec_filled, nfront = sm.nfront;
+  if (filled == 0 || sm.spec_iter != it) {
+    if (tid == 0) c->status = INPAINT_ERR_INTERNAL;  // p^ not in Omega, or stale speculation
+    __syncthreads();
     return false;
   }
   const uint32_t ssd = (uint32_t)(best >> 32);
@@ -319,60 +439,37 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const int qx = q % W, qy = q / W;
 
   // copy the unknown in-image part of Psi_p^ from Psi_q~
-  int my_filled = 0;
   for (int i = tid; i < P * P; i += nt) {
+    if (!sm.filled[i]) continue;
     const int dy = i / P - R, dx = i % P - R;
     const int l = (RB + dy) * NS + RB + dx;
-    uint8_t f = 0;
-    if (sm.om[l] == 1) {
-      const int tx = px + dx, ty = py + dy;
-      const uint32_t w = __ldcg(&s.img[(size_t)(qy + dy) * s.pitch + qx + dx]);
-      const uint8_t g = (uint8_t)luma_word(w);
-      const size_t t = (size_t)ty * W + tx;
-      s.img[(size_t)ty * s.pitch + tx] = w;
-      s.gray[t] = g;
-      s.conf[t] = cp;
-      s.omega[t] = 0;
-      sm.om[l] = 0;
-      sm.gr[l] = g;
-      f = 1;
-      ++my_filled;
-    }
-    sm.filled[i] = f;
+    const int tx = px + dx, ty = py + dy;
+    const uint32_t w = __ldcg(&s.img[(size_t)(qy + dy) * s.pitch + qx + dx]);
+    const uint8_t g = (uint8_t)luma_word(w);
+    const size_t t = (size_t)ty * W + tx;
+    s.img[(size_t)ty * s.pitch + tx] = w;
+    s.gray[t] = g;
+    s.conf[t] = cp;
+    s.omega[t] = 0;
+    sm.gr[l] = g;
   }
-  const int filled = block_sum_int(my_filled, sm.red32);
-  if (filled == 0 || spec_iter != it || spec_filled != filled) {
-    if (tid == 0) c->status = INPAINT_ERR_INTERNAL;  // p^ not in Omega, or stale speculation
-    return false;
-  }
+  __syncthreads();
   const int nx_in = min(px + R, W - 1) - max(px - R, 0) + 1;
   const int ny_in = min(py + R, H - 1) - max(py - R, 0) + 1;
   const int n_known = nx_in * ny_in - filled;
 
-  // isophotes of the new grey levels; integral image of the filled flags
+  // isophotes of the new grey levels
   stage_isophotes<R>(sm);
-  if (tid < 32) {
-    constexpr int P1 = P + 1;
-    for (int v = tid; v <= P; v += 32) {
-      sm.fsat[v] = 0;
-      sm.fsat[v * P1] = 0;
-    }
-    __syncwarp();
-    for (int v = tid; v < P; v += 32) {
-      int run = 0;
-      for (int u = 0; u < P; ++u) {
-        run += sm.filled[v * P + u];
-        sm.fsat[(v + 1) * P1 + u + 1] = run;
-      }
-    }
-    __syncwarp();
-    for (int u = tid + 1; u <= P; u += 32)
-      for (int v = 2; v <= P; ++v) sm.fsat[v * P1 + u] += sm.fsat[(v - 1) * P1 + u];
-  }
   __syncthreads();
 
   // priorities of the window (front pixels from the compact list, spread
-  // over the sub-partitions; the others get key 0) and validity counts
+  // over the sub-partitions; the others get key 0) and validity counts;
+  // new keys also go to the cached level-0 tiles
+  const int ctx0 = ca.tx0, cty0 = ca.ty0, cntx = ca.ntx;
+  auto cache_prio = [&](int x, int y, unsigned long long key) {
+    const int t = (y / kT0 - cty0) * cntx + (x / kT0 - ctx0);
+    ca.tp[t * (kT0 * kT0) + (y & (kT0 - 1)) * kT0 + (x & (kT0 - 1))] = key;
+  };
   int newly = 0;
   const int nlist = (nfront + 127) & ~127;
   for (int t = tid; t < nlist + NW * NW + NC * NC; t += nt) {
@@ -386,15 +483,20 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       const double cc = sm.sC[i];
       const int nrm = sm.snrm[i];
       const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
-      const size_t p = (size_t)(py + wy) * W + px + wx;
-      s.prio[p] = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
+      const int x = px + wx, y = py + wy;
+      const size_t p = (size_t)y * W + x;
+      const unsigned long long key = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
+      s.prio[p] = key;
       s.pconf[p] = cc;
+      cache_prio(x, y, key);
     } else if (t < nlist + NW * NW) {
       const int i = t - nlist;
       if (sm.snrm[i] != kSpecNotFront) continue;  // outside, or a front pixel
-      const size_t p = (size_t)(py + i / NW - R2) * W + px + i % NW - R2;
+      const int x = px + i % NW - R2, y = py + i / NW - R2;
+      const size_t p = (size_t)y * W + x;
       s.prio[p] = 0ull;
       s.pconf[p] = 0.0;
+      cache_prio(x, y, 0ull);
     } else {
       const int j = t - nlist - NW * NW;
       const int wy = j / NC - 2 * R, wx = j % NC - 2 * R;
@@ -406,23 +508,81 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       const int dec = sm.fsat[(v1 + 1) * P1 + u1 + 1] - sm.fsat[v0 * P1 + u1 + 1] -
                       sm.fsat[(v1 + 1) * P1 + u0] + sm.fsat[v0 * P1 + u0];
       if (dec) {
-        const size_t qi = (size_t)y * W + x;
-        const int nv = __ldcg(&s.count[qi]) - dec;
-        s.count[qi] = nv;
+        const int nv = ca.cnt[j] - dec;
+        s.count[(size_t)y * s.pitch + x] = nv;
         if (nv == 0 && x >= s.cx0 && x <= s.cx1 && y >= s.cy0 && y <= s.cy1) ++newly;
       }
     }
   }
-  newly = block_sum_int(newly, sm.red32);
+  newly = block_sum_int(newly, sm.red32);  // includes __syncthreads
 
-  // tiles over the window, then the next target (into shared memory; the
-  // control block is written by update_finish)
-  block_refresh_tiles(s, max(0, px - R2), min(W - 1, px + R2), max(0, py - R2), min(H - 1, py + R2));
+  // level-0 tiles from the cached keys, then level-1, then the best
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int t = wid; t < ca.ntx * ca.nty; t += nw) {
+    const int tx = ca.tx0 + t % ca.ntx, ty = ca.ty0 + t / ca.ntx;
+    unsigned long long k = 0ull;
+    int idx = 0x7fffffff;
+#pragma unroll
+    for (int r8 = 0; r8 < kT0 * kT0 / 32; ++r8) {
+      const int j = lane + 32 * r8;
+      const int x = tx * kT0 + (j & (kT0 - 1)), y = ty * kT0 + j / kT0;
+      const unsigned long long kk = ca.tp[t * (kT0 * kT0) + j];
+      const int ii = y * W + x;
+      if (prio_better(kk, ii, k, idx)) {
+        k = kk;
+        idx = ii;
+      }
+    }
+    warp_best_prio(k, idx);
+    if (lane == 0) {
+      s.tiles0[ty * s.t0x + tx].key = k;
+      s.tiles0[ty * s.t0x + tx].idx = idx;
+      const int u = (ty / kT1 - ca.uy0) * ca.nux + (tx / kT1 - ca.ux0);
+      PrioBest& e = ca.t0c[u * (kT1 * kT1) + (ty & (kT1 - 1)) * kT1 + (tx & (kT1 - 1))];
+      e.key = k;
+      e.idx = idx;
+    }
+  }
+  __syncthreads();
+  for (int u = wid; u < ca.nux * ca.nuy; u += nw) {
+    const int ux = ca.ux0 + u % ca.nux, uy = ca.uy0 + u / ca.nux;
+    unsigned long long k = 0ull;
+    int idx = 0x7fffffff;
+#pragma unroll
+    for (int r8 = 0; r8 < kT1 * kT1 / 32; ++r8) {
+      const PrioBest& e = ca.t0c[u * (kT1 * kT1) + lane + 32 * r8];
+      if (prio_better(e.key, e.idx, k, idx)) {
+        k = e.key;
+        idx = e.idx;
+      }
+    }
+    warp_best_prio(k, idx);
+    if (lane == 0) {
+      s.tiles1[uy * s.t1x + ux].key = k;
+      s.tiles1[uy * s.t1x + ux].idx = idx;
+      if (ca.t1n) {
+        ca.t1c[uy * s.t1x + ux].key = k;
+        ca.t1c[uy * s.t1x + ux].idx = idx;
+      }
+    }
+  }
+  __syncthreads();
   remaining -= filled;
   if (tid < 32) {
     unsigned long long k = 0ull;
     int idx = 0x7fffffff;
-    if (remaining > 0) warp_global_best(s, k, idx);
+    if (remaining > 0) {
+      if (ca.t1n) {
+        for (int j = lane; j < ca.t1n; j += 32)
+          if (prio_better(ca.t1c[j].key, ca.t1c[j].idx, k, idx)) {
+            k = ca.t1c[j].key;
+            idx = ca.t1c[j].idx;
+          }
+        warp_best_prio(k, idx);
+      } else {
+        warp_global_best(s, k, idx);
+      }
+    }
     if (tid == 0) {
       sm.next_key = k;
       sm.next_idx = idx;
