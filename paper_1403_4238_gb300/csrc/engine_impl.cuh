@@ -278,15 +278,20 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     // validity counts of its candidates, on one mbarrier
     auto issue = [&](int b, uint32_t* st, uint64_t* bar, bool pixels) {
       const int gx = b % ncg, gy = b / ncg;
-      asm volatile("fence.proxy.async;" ::: "memory");
+      // (the stage's previous generic reads are ordered before this by the
+      // block barrier that ends every batch)
       mbar_expect_tx(bar, (uint32_t)((pixels ? G::BW * G::BH * 4 : 0) + kEngCountW * B * 4));
       if (pixels) tma_load_2d(st, map, xb - R + 128 * gx, s.cy0 + B * gy - R, bar);
       tma_load_2d(reinterpret_cast<uint8_t*>(st) + G::PIX_BYTES, cmap, xb - G::COFF + 128 * gx,
                   s.cy0 + B * gy, bar);
     };
+    // thread 0 grabs one batch ahead (nxt), so the counter's latency hides
+    // behind a batch of compute
+    int nxt = nbatch;
     if (tid == 0) {
       tl.bcur = b0 < nbatch ? b0 : (nbatch > nst ? grab() : nbatch);
       if (tl.bcur < nbatch) issue(tl.bcur, stage0, &tl.full[0], tl.bcur != b0 || need0);
+      if (tl.bcur < nbatch && nbatch > nst) nxt = grab();
     }
     // target patch: one thread per pixel, then the row masks
     if (tid < P * P) {
@@ -313,9 +318,12 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     int nproc = 0;
     for (int b = tl.bcur; b < nbatch;) {
       if (tid == 0) {
-        const int nb = nbatch > nst ? grab() : nbatch;
+        const int nb = nxt;
         tl.bnx[cur] = nb;  // read by all after the barrier at the end of this batch
-        if (nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1], true);
+        if (nb < nbatch) {
+          issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1], true);
+          nxt = grab();  // consumed at the top of the next batch
+        }
       }
       const int gx = b % ncg, gy = b / ncg;
       const int qx0 = xb + 128 * gx + lane * 4, qy0 = s.cy0 + B * gy + warp * SRW;

@@ -267,23 +267,46 @@ __device__ void update_prefetch(const ImgState& s, UpdCache<R>& ca, int first) {
     const int x = px + j % NC - 2 * R, y = py + j / NC - 2 * R;
     ca.cnt[j] = (x >= 0 && x < W && y >= 0 && y < H) ? __ldcg(&s.count[(size_t)y * s.pitch + x]) : 0;
   }
-  for (int e = threadIdx.x - first; e < ntx * nty * kT0 * kT0; e += blockDim.x - first) {
-    const int t = e / (kT0 * kT0), j = e % (kT0 * kT0);
-    const int x = (tx0 + t % ntx) * kT0 + (j & (kT0 - 1)), y = (ty0 + t / ntx) * kT0 + j / kT0;
-    ca.tp[e] = (x < W && y < H) ? __ldcg(&s.prio[(size_t)y * W + x]) : 0ull;
-  }
-  for (int e = threadIdx.x - first; e < nux * nuy * kT1 * kT1; e += blockDim.x - first) {
-    const int u = e / (kT1 * kT1), j = e % (kT1 * kT1);
-    const int tx = (ux0 + u % nux) * kT1 + (j & (kT1 - 1)), ty = (uy0 + u / nux) * kT1 + j / kT1;
-    PrioBest b;
-    b.key = 0ull;
-    b.idx = 0x7fffffff;
-    b.pad = 0;
-    if (tx < s.t0x && ty < s.t0y) {
-      b.key = __ldcg(&s.tiles0[ty * s.t0x + tx].key);
-      b.idx = __ldcg(&s.tiles0[ty * s.t0x + tx].idx);
+  {
+    // eight loads in flight per thread
+    constexpr int U = 8;
+    const int n = ntx * nty * kT0 * kT0, step = (int)blockDim.x - first;
+    for (int e0 = threadIdx.x - first; e0 < n; e0 += U * step) {
+      unsigned long long v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * step;
+        const int t = e / (kT0 * kT0), j = e % (kT0 * kT0);
+        const int x = (tx0 + t % ntx) * kT0 + (j & (kT0 - 1)), y = (ty0 + t / ntx) * kT0 + j / kT0;
+        v[u] = (e < n && x < W && y < H) ? __ldcg(&s.prio[(size_t)y * W + x]) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (e0 + u * step < n) ca.tp[e0 + u * step] = v[u];
     }
-    ca.t0c[e] = b;
+  }
+  {
+    constexpr int U = 4;
+    const int n = nux * nuy * kT1 * kT1, step = (int)blockDim.x - first;
+    for (int e0 = threadIdx.x - first; e0 < n; e0 += U * step) {
+      PrioBest b[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int e = e0 + k * step;
+        const int u = e / (kT1 * kT1), j = e % (kT1 * kT1);
+        const int tx = (ux0 + u % nux) * kT1 + (j & (kT1 - 1)), ty = (uy0 + u / nux) * kT1 + j / kT1;
+        b[k].key = 0ull;
+        b[k].idx = 0x7fffffff;
+        b[k].pad = 0;
+        if (e < n && tx < s.t0x && ty < s.t0y) {
+          b[k].key = __ldcg(&s.tiles0[ty * s.t0x + tx].key);
+          b[k].idx = __ldcg(&s.tiles0[ty * s.t0x + tx].idx);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (e0 + k * step < n) ca.t0c[e0 + k * step] = b[k];
+    }
   }
   if (n1 <= kT1Cache)
     for (int e = threadIdx.x - first; e < n1; e += blockDim.x - first) {
