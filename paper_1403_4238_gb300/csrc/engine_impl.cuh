@@ -107,12 +107,71 @@ __device__ inline void compute_rows(const uint32_t* __restrict__ stage, int row0
   }
 }
 
+// Two-row batches (SRW = 2): half-warps take two adjacent candidate rows and
+// each lane eight adjacent candidates (columns (lane & 15) * 8 ...), so both
+// half-warps use the same target row at a time: the row-mask branch stays
+// warp-uniform and costs half as much per evaluation as with four candidates.
+template <int R>
+__device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row, int col,
+                                     const uint32_t* __restrict__ tgt,
+                                     const uint32_t* __restrict__ rowmask, uint32_t (&acc)[8]) {
+  using G = EngGeom<R, 2>;
+  constexpr int P = G::P, BW = G::BW, N8 = (8 + P - 1 + 3) & ~3;
+  static_assert(15 * 8 + N8 <= BW, "row strip must stay inside the tile");
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = 0;
+#pragma unroll 1
+  for (int dy = 0; dy < P; ++dy) {
+    const uint32_t m = rowmask[dy];
+    if (m == 0) continue;
+    uint32_t r[N8];
+    const uint4* sp = reinterpret_cast<const uint4*>(stage + (row + dy) * BW + col);
+#pragma unroll
+    for (int i = 0; i < N8 / 4; ++i) {
+      const uint4 v = sp[i];
+      r[4 * i] = v.x;
+      r[4 * i + 1] = v.y;
+      r[4 * i + 2] = v.z;
+      r[4 * i + 3] = v.w;
+    }
+    uint32_t t[G::TP];
+    const uint4* tp = reinterpret_cast<const uint4*>(tgt + dy * G::TP);
+#pragma unroll
+    for (int i = 0; i < G::TP / 4; ++i) {
+      const uint4 v = tp[i];
+      t[4 * i] = v.x;
+      t[4 * i + 1] = v.y;
+      t[4 * i + 2] = v.z;
+      t[4 * i + 3] = v.w;
+    }
+    if (m == G::FULL) {
+#pragma unroll
+      for (int dx = 0; dx < P; ++dx) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
+          acc[k] = __dp4a(d, d, acc[k]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int dx = 0; dx < P; ++dx) {
+        if (m & (1u << dx)) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
+            acc[k] = __dp4a(d, d, acc[k]);
+          }
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- kernel
 
 struct EngSmemTail {
   uint64_t full[2];  // TMA completion barriers of the two stages
-  int bcur;          // first search batch of this CTA in the round
-  int bnx[2];        // next batch, written by thread 0 in alternate slots
   unsigned long long red64[32];
   int red32[32];
   int flag;
@@ -240,20 +299,16 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   const int ncg = s.cx1 >= s.cx0 ? (s.cx1 - xb + 128) / 128 : 0;
   const int nrb = s.cy1 >= s.cy0 ? (s.cy1 - s.cy0 + B) / B : 0;
   const int nbatch = ncg * nrb;
-  // Roles: CTAs [0, ns) search.  The last CTA of the team is the leader: it
-  // runs the speculative phase of each iteration while the others search,
-  // waits for their keys, applies the update and publishes the next round.
-  // On an image with many batches per CTA the leader searches too; a CTA
-  // that neither searches nor leads idles until the image is done.
-  const bool lead_searches = tsize == 1 || nbatch >= 4 * tsize;
-  const int ns = lead_searches ? tsize : min(tsize - 1, nbatch);
+  // Roles: CTAs [0, ns) search, batch b going to CTA b mod ns (batches cost
+  // alike).  The last CTA of the team is the leader: it runs the speculative
+  // phase of each iteration while the others search, waits for their keys,
+  // applies the update and publishes the next round; it searches only in a
+  // team of one.  A CTA that neither searches nor leads idles until the image
+  // is done.
+  const bool lead_searches = tsize == 1;
+  const int ns = lead_searches ? 1 : min(tsize - 1, nbatch);
   const bool leader = rank == tsize - 1;
   const bool searcher = rank < ns;
-  // Batches [0, nst) go one per searcher (the leader, busy with the
-  // speculative phase first, takes none of them); the rest are handed out
-  // in arrival order from the team counter, so a CTA that starts late or
-  // runs slow takes fewer.
-  const int nst = min(nbatch, lead_searches && tsize > 1 ? ns - 1 : ns);
   const unsigned n_wait = (unsigned)(lead_searches ? ns - 1 : ns);
   bool resident = false;  // stage0 holds this CTA's only batch of the image
   if (tid == 0) {
@@ -267,10 +322,8 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
 
   // One search round for target (px, py): this CTA's batches; returns its
   // best key.  Whole block.
-  auto grab = [&]() -> int { return nst + (int)atomicAdd(&tc->next, 1u); };
   auto search_round = [&](int px, int py) -> unsigned long long {
-    const bool has_static = rank < nst && !(leader && lead_searches && tsize > 1);
-    const int b0 = has_static ? rank : nbatch;
+    const int b0 = rank < ns ? rank : nbatch;
     const bool need0 = !resident ||
                        (abs(prev_px - (xb + 128 * (b0 % max(ncg, 1)) + 64)) <= 64 + 2 * R + 4 &&
                         abs(prev_py - (s.cy0 + B * (b0 / max(ncg, 1)) + B / 2)) <= B / 2 + 2 * R + 1);
@@ -285,14 +338,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       tma_load_2d(reinterpret_cast<uint8_t*>(st) + G::PIX_BYTES, cmap, xb - G::COFF + 128 * gx,
                   s.cy0 + B * gy, bar);
     };
-    // thread 0 grabs one batch ahead (nxt), so the counter's latency hides
-    // behind a batch of compute
-    int nxt = nbatch;
-    if (tid == 0) {
-      tl.bcur = b0 < nbatch ? b0 : (nbatch > nst ? grab() : nbatch);
-      if (tl.bcur < nbatch) issue(tl.bcur, stage0, &tl.full[0], tl.bcur != b0 || need0);
-      if (tl.bcur < nbatch && nbatch > nst) nxt = grab();
-    }
+    if (tid == 0 && b0 < nbatch) issue(b0, stage0, &tl.full[0], need0);
     // target patch: one thread per pixel, then the row masks
     if (tid < P * P) {
       const int tx = px + tid % P - R, ty = py + tid / P - R;
@@ -316,45 +362,56 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     int cur = 0;
     bool ok = true;
     int nproc = 0;
-    for (int b = tl.bcur; b < nbatch;) {
-      if (tid == 0) {
-        const int nb = nxt;
-        tl.bnx[cur] = nb;  // read by all after the barrier at the end of this batch
-        if (nb < nbatch) {
-          issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1], true);
-          nxt = grab();  // consumed at the top of the next batch
-        }
-      }
+    for (int b = b0; b < nbatch; b += ns) {
+      const int nb = b + ns;
+      if (tid == 0 && nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1], true);
       const int gx = b % ncg, gy = b / ncg;
       const int qx0 = xb + 128 * gx + lane * 4, qy0 = s.cy0 + B * gy + warp * SRW;
       const bool got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
       if (cur) ph1 ^= 1; else ph0 ^= 1;
       const uint32_t* stg = cur ? stage1 : stage0;
-      uint32_t acc[SRW][4];
-      compute_rows<R, SRW>(stg, warp * SRW, tgt, rowmask, acc);
       const int* cst = reinterpret_cast<const int*>(reinterpret_cast<const uint8_t*>(stg) + G::PIX_BYTES);
+      if constexpr (SRW == 2) {
+        // lane: candidate row warp*2 + lane/16, columns (lane & 15)*8 + [0, 8)
+        const int lrow = warp * 2 + (lane >> 4), lcol = (lane & 15) * 8;
+        uint32_t acc[8];
+        compute_rows8<R>(stg, lrow, lcol, tgt, rowmask, acc);
+        const int qy = s.cy0 + B * gy + lrow;
 #pragma unroll
-      for (int o = 0; o < SRW; ++o)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int qx = qx0 + k, qy = qy0 + o;
+        for (int k = 0; k < 8; ++k) {
+          const int qx = xb + 128 * gx + lcol + k;
           const bool in = qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1;
-          if (in && cst[(warp * SRW + o) * kEngCountW + G::COFF + lane * 4 + k] == 0) {
+          if (in && cst[lrow * kEngCountW + G::COFF + lcol + k] == 0) {
             const unsigned idx = (unsigned)(qy * s.W + qx);
-            const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
+            const unsigned long long key = ((unsigned long long)acc[k] << 32) | idx;
             best = key < best ? key : best;
           }
         }
+      } else {
+        uint32_t acc[SRW][4];
+        compute_rows<R, SRW>(stg, warp * SRW, tgt, rowmask, acc);
+#pragma unroll
+        for (int o = 0; o < SRW; ++o)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int qx = qx0 + k, qy = qy0 + o;
+            const bool in = qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1;
+            if (in && cst[(warp * SRW + o) * kEngCountW + G::COFF + lane * 4 + k] == 0) {
+              const unsigned idx = (unsigned)(qy * s.W + qx);
+              const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
+              best = key < best ? key : best;
+            }
+          }
+      }
       ++nproc;
       if (__syncthreads_or(!got)) {  // a bounded wait gave up: stop uniformly
         ok = false;
-        if (tl.bnx[cur] < nbatch) {
+        if (nb < nbatch) {
           mbar_wait(&tl.full[cur ^ 1], cur ? ph0 : ph1, limit);
           if (cur) ph0 ^= 1; else ph1 ^= 1;
         }
         break;
       }
-      b = tl.bnx[cur];
       cur ^= 1;
     }
     // the tile stays resident when it was this CTA's only batch (the leader's
@@ -392,7 +449,6 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       __syncthreads();
       if (tid == 0) {
         tc->arrive = 0u;
-        tc->next = 0u;
         st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
         tl.stop = stop;
         tl.px = npx;

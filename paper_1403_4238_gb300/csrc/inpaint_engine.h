@@ -15,8 +15,7 @@ constexpr int kEngCountW = 132;  // count words staged per batch row (128 + alig
 struct TeamCtl {
   unsigned long long pub;  // epoch | next px | next py | stop (release-published)
   unsigned arrive;         // searchers arrived in the current iteration
-  unsigned next;           // search batches handed out beyond the static first ones
-  unsigned pad[28];        // keep teams on separate 128-byte lines
+  unsigned pad[29];        // keep teams on separate 128-byte lines
 };
 
 struct EngineArgs {
