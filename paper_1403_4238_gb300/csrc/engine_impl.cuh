@@ -377,11 +377,21 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
         uint32_t acc[8];
         compute_rows8<R>(stg, lrow, lcol, tgt, rowmask, acc);
         const int qy = s.cy0 + B * gy + lrow;
+        int cw[12];  // counts of this lane's candidates (vector loads, 16-byte aligned)
+        const int4* cp4 = reinterpret_cast<const int4*>(cst + lrow * kEngCountW + lcol);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const int4 v = cp4[i];
+          cw[4 * i] = v.x;
+          cw[4 * i + 1] = v.y;
+          cw[4 * i + 2] = v.z;
+          cw[4 * i + 3] = v.w;
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int qx = xb + 128 * gx + lcol + k;
           const bool in = qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1;
-          if (in && cst[lrow * kEngCountW + G::COFF + lcol + k] == 0) {
+          if (in && cw[G::COFF + k] == 0) {
             const unsigned idx = (unsigned)(qy * s.W + qx);
             const unsigned long long key = ((unsigned long long)acc[k] << 32) | idx;
             best = key < best ? key : best;
@@ -391,17 +401,23 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
         uint32_t acc[SRW][4];
         compute_rows<R, SRW>(stg, warp * SRW, tgt, rowmask, acc);
 #pragma unroll
-        for (int o = 0; o < SRW; ++o)
+        for (int o = 0; o < SRW; ++o) {
+          int cw[8];  // counts of this lane's candidates (vector loads, 16-byte aligned)
+          const int4* cp4 = reinterpret_cast<const int4*>(cst + (warp * SRW + o) * kEngCountW + lane * 4);
+          const int4 v0 = cp4[0], v1 = cp4[1];
+          cw[0] = v0.x; cw[1] = v0.y; cw[2] = v0.z; cw[3] = v0.w;
+          cw[4] = v1.x; cw[5] = v1.y; cw[6] = v1.z; cw[7] = v1.w;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int qx = qx0 + k, qy = qy0 + o;
             const bool in = qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1;
-            if (in && cst[(warp * SRW + o) * kEngCountW + G::COFF + lane * 4 + k] == 0) {
+            if (in && cw[G::COFF + k] == 0) {
               const unsigned idx = (unsigned)(qy * s.W + qx);
               const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
               best = key < best ? key : best;
             }
           }
+        }
       }
       ++nproc;
       if (__syncthreads_or(!got)) {  // a bounded wait gave up: stop uniformly

@@ -7,24 +7,27 @@
 //   A2   = sum_d m(d) sum_c t'_c(d)^2                       (one integer)
 //   X(q) = sum_c sum_d [m(d) t'_c(d)] s'_c(q+d)             (3 correlations)
 //   S(q) = sum_d m(d) sq(q+d),  sq = sum_c s'_c^2 <= 49152   (split as
-//          sq = 256 hi + lo with hi, lo < 256: two correlations)
+//          sq = 256 hi + lo with hi, lo < 256, weights 256 m and m)
 // Every product of two BF16 integers is exact and every partial sum is an
-// integer of magnitude below 2^24 (|X| <= 17^2 * 3 * 128^2, S parts below
-// 17^2 * 255), so the FP32 accumulators hold exact integers and the SSD equals
-// the CUDA-core form's bit for bit.
+// integer of magnitude below 2^24 (|X| <= 17^2 * 3 * 128^2, S <= 17^2 * 49152),
+// so the FP32 accumulators hold exact integers and the SSD equals the
+// CUDA-core form's bit for bit.
 //
 // The correlations run as tcgen05 MMAs (kind::f16, BF16 operands in shared
 // memory, FP32 accumulators in tensor memory) with no im2col copy:
 //  * A (M = 128): row a is a block of 8 consecutive candidates (64 blocks of
-//    one candidate row, then 64 of the next); it reads the plane row directly,
-//    row a starting 16 bytes after row a - 1.  That is the canonical
-//    no-swizzle K-major layout with a 16-byte stride between the two K core
-//    matrices of an MMA (consecutive rows overlap in memory).
+//    one candidate row, then 64 of the next); it reads a plane row directly,
+//    row a starting 16 bytes after row a - 1 (the canonical no-swizzle
+//    K-major layout; consecutive rows overlap in memory).  The two 8-element
+//    K halves of an MMA are two "items" (plane, 8-tap chunk): the leading
+//    byte offset between the K core matrices is simply the distance between
+//    the two items, so an MMA can pair chunks of different planes and only
+//    ceil((P + 7) / 8) chunks per plane are needed.
 //  * B (N = 8 RP for RP candidate row pairs): the Toeplitz matrix of target
 //    rows, B[8k + b][j] = T[rho - 2k][j - b], for the plane row rho at which A
-//    starts.  One MMA per (rho, K chunk, plane) updates all RP row pairs; B
-//    for rho + 2 is B for rho shifted by one 8-row group, so one strip of
-//    groups per (plane, K chunk, parity of rho) serves every rho.
+//    starts.  One MMA per (rho, item pair) updates all RP row pairs; B for
+//    rho + 2 is B for rho shifted by one 8-row group, so one half-strip of
+//    groups per (plane, chunk, parity of rho) serves every rho.
 // A tile is RC candidate rows x TS candidate columns.  Per CTA the tiles
 // run as a pipeline: one control warp issues the TMA load of tile i+1's RGBA
 // rows into a staging buffer and the MMAs of tile i into one of two tensor-
@@ -50,7 +53,10 @@ struct TcGeom {
   static constexpr int RC = R == 8 ? 4 : 8;            // candidate rows per tile
   static constexpr int RP = RC / 2;                    // candidate row pairs
   static constexpr int N = 8 * RP;                     // MMA N
-  static constexpr int KC = (P + 22) / 16;             // K chunks: taps j = b + dx < P + 7
+  static constexpr int NC8 = (P + 14) / 8;             // 8-tap chunks: taps j = b + dx < P + 7
+  static constexpr int NX = 3 * NC8;                   // cross-term items (channel, chunk)
+  static constexpr int NXP = (NX + 1) / 2;             // cross-term MMAs per plane row
+  static constexpr int NHS = 5 * NC8 * 2 + 2;          // B half-strips (+ a zero pair)
   static constexpr int NR = RC + P - 1;                // plane rows of a tile
   static constexpr int NRHO = RC + P - 2;              // A start rows
   static constexpr int TMAX = (NRHO - 1) / 2;
@@ -58,18 +64,18 @@ struct TcGeom {
   static constexpr int TS = (kTcPlaneW + 1 - P) & ~7;  // candidate columns per tile
   static constexpr int STG_BYTES = 2 * NR * 256 * 4;   // two 256-word TMA boxes
   static constexpr int PLANE_BYTES = NR * kTcPlaneW * 2 + 128;
-  static constexpr int B_BYTES = 4 * KC * 2 * GB * 256;
+  static constexpr int B_BYTES = NHS * GB * 128;
   static constexpr int OFF_PL = STG_BYTES;
   static constexpr int OFF_B = OFF_PL + 5 * PLANE_BYTES;
   static constexpr int OFF_T = OFF_B + B_BYTES;  // int16 T[4][P * P]
   static constexpr int OFF_MISC = (OFF_T + 4 * P * P * 2 + 15) & ~15;
   static constexpr int RAW = OFF_MISC + 384 + 128;  // + base alignment
   static constexpr int SMEM = RAW < kTcMinSmem ? kTcMinSmem : RAW;
-  static constexpr uint32_t ACC = 3 * N;             // columns of one accumulator set
+  static constexpr uint32_t ACC = 2 * N;             // columns of one accumulator set (X, S)
   static constexpr uint32_t TMEM_COLS = 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128 : 256;
   static_assert(RP <= 8, "at most two row pairs per worker warp");
   static_assert(N % 16 == 0 && N <= 256, "M = 128 needs N a multiple of 16");
-  static_assert(KC * 16 >= P + 7, "K chunks must cover every tap");
+  static_assert(NC8 * 8 >= P + 7, "chunks must cover every tap");
   static_assert(2 * ACC <= 256, "two accumulator sets in 256 columns");
   static_assert(SMEM <= 227 * 1024, "tile does not fit in shared memory");
 };
@@ -250,28 +256,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_search_tc(ImgState s, int nx,
                                 G::NR * kTcPlaneW * 2)[i % 32] = 0u;
   __syncthreads();
 
-  // B strips, one 16-byte core-matrix row per step: row rr of strip
-  // ((kappa * KC + kc) * 2 + par), group gi, core matrix cm (K half), row b.
-  constexpr int NBR = 4 * G::KC * 2 * G::GB * 16;
+  // B half-strips, one 16-byte core-matrix row per step: row rr of
+  // half-strip hs = (kappa * NC8 + c) * 2 + par (the last two all zeros),
+  // group gi, row b; kappa 0-2 channels (T'), 3 the weights 256 m, 4 m.
+  constexpr int NBR = G::NHS * G::GB * 8;
   for (int rr = tid; rr < NBR; rr += kTcThreads) {
-    const int b = rr & 7, cm = (rr >> 3) & 1;
-    int rest = rr >> 4;
+    const int b = rr & 7;
+    int rest = rr >> 3;
     const int gi = rest % G::GB;
-    rest /= G::GB;
-    const int par = rest & 1;
-    rest >>= 1;
-    const int kc = rest % G::KC, kap = rest / G::KC;
-    const int dy = par - 2 * (gi - G::TMAX);
+    const int hs = rest / G::GB;
     uint32_t wv[4] = {0u, 0u, 0u, 0u};
-    if (dy >= 0 && dy < P) {
-      const int dx0 = 16 * kc + 8 * cm - b;
-      const int16_t* trow = tv + kap * P * P + dy * P;
+    if (hs < 5 * G::NC8 * 2) {
+      const int par = hs & 1, c = (hs >> 1) % G::NC8, kap = (hs >> 1) / G::NC8;
+      const int dy = par - 2 * (gi - G::TMAX);
+      if (dy >= 0 && dy < P) {
+        const int dx0 = 8 * c - b;
+        const int16_t* trow = tv + (kap < 3 ? kap : 3) * P * P + dy * P;
+        const int scale = kap == 3 ? 256 : 1;
 #pragma unroll
-      for (int jj = 0; jj < 8; jj += 2) {
-        const int d0 = dx0 + jj, d1 = d0 + 1;
-        const int v0 = (d0 >= 0 && d0 < P) ? trow[d0] : 0;
-        const int v1 = (d1 >= 0 && d1 < P) ? trow[d1] : 0;
-        wv[jj >> 1] = bf16_int(v0) | (bf16_int(v1) << 16);
+        for (int jj = 0; jj < 8; jj += 2) {
+          const int d0 = dx0 + jj, d1 = d0 + 1;
+          const int v0 = (d0 >= 0 && d0 < P) ? scale * trow[d0] : 0;
+          const int v1 = (d1 >= 0 && d1 < P) ? scale * trow[d1] : 0;
+          wv[jj >> 1] = bf16_int(v0) | (bf16_int(v1) << 16);
+        }
       }
     }
     *reinterpret_cast<uint4*>(sm + G::OFF_B + rr * 16) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
@@ -294,8 +302,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_search_tc(ImgState s, int nx,
   const int a2 = *a2_slot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(G::N >> 3) << 17) |
                          ((uint32_t)(128 >> 4) << 24);
-  const uint64_t adesc0 = tc_desc(smem_addr(sm + G::OFF_PL), 16, 128);
-  const uint64_t bdesc0 = tc_desc(smem_addr(sm + G::OFF_B), 128, 256);
+  // base descriptors (leading byte offsets are added per item pair)
+  const uint64_t adesc0 = tc_desc(smem_addr(sm + G::OFF_PL), 0, 128);
+  const uint64_t bdesc0 = tc_desc(smem_addr(sm + G::OFF_B), 0, 128);
   const int wq = warp & 3, kh = warp >> 2;  // TMEM lane quarter; row pairs kh, kh + 4, ...
   const int a = 32 * wq + lane, a_row = a >> 6, a_blk = a & 63;
   constexpr int KPW = (G::RP + 3) / 4;  // row pairs per worker warp
@@ -352,30 +361,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_search_tc(ImgState s, int nx,
         const uint32_t dcol = tmem + (uint32_t)((i & 1) * G::ACC);
         const uint32_t a_lo = (uint32_t)adesc0, a_hi = (uint32_t)(adesc0 >> 32);
         const uint32_t b_lo = (uint32_t)bdesc0, b_hi = (uint32_t)(bdesc0 >> 32);
-        // descriptor units are 16 bytes; every offset below is a constant
+        // item (kappa, c): A at plane kappa, column 8c; B half-strip
+        // (kappa * NC8 + c) * 2 + parity.  Descriptor units are 16 bytes; the
+        // leading byte offset sits at bit 16.  Every offset is a constant.
+        constexpr uint32_t PLU = G::PLANE_BYTES / 16, HSU = G::GB * 8;  // plane, half-strip
+        auto a_item = [&](int kap, int c) { return (uint32_t)(kap * PLU + c); };
+        auto b_item = [&](int kap, int c) { return (uint32_t)((kap * G::NC8 + c) * 2 * HSU); };
 #pragma unroll
         for (int rho = 0; rho < G::NRHO; ++rho) {
+          const uint32_t arow = (uint32_t)(rho * (kTcPlaneW * 2 / 16));
+          const uint32_t bsh = (uint32_t)(((rho & 1) * G::GB + G::TMAX - (rho >> 1)) * 8);
 #pragma unroll
-          for (int kc = 0; kc < G::KC; ++kc) {
-            const uint32_t ao = a_lo + (uint32_t)(rho * (kTcPlaneW * 2 / 16) + 2 * kc);
-            const int bstrip = (rho & 1) * G::GB + G::TMAX - (rho >> 1);  // + (kappa*KC+kc)*2*GB
-            if (rho == 0 && kc == 0) {
-              tc_mma_lo<0>(dcol, ao, a_hi, b_lo + (uint32_t)(((0 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
-              tc_mma_lo<0>(dcol + G::N, ao + 3 * (G::PLANE_BYTES / 16), a_hi,
-                           b_lo + (uint32_t)(((3 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
-              tc_mma_lo<0>(dcol + 2 * G::N, ao + 4 * (G::PLANE_BYTES / 16), a_hi,
-                           b_lo + (uint32_t)(((3 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
-            } else {
-              tc_mma_lo<1>(dcol, ao, a_hi, b_lo + (uint32_t)(((0 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
-              tc_mma_lo<1>(dcol + G::N, ao + 3 * (G::PLANE_BYTES / 16), a_hi,
-                           b_lo + (uint32_t)(((3 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
-              tc_mma_lo<1>(dcol + 2 * G::N, ao + 4 * (G::PLANE_BYTES / 16), a_hi,
-                           b_lo + (uint32_t)(((3 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
+          for (int pi = 0; pi < G::NXP; ++pi) {  // cross-term item pairs into X
+            const int i1 = 2 * pi, i2 = 2 * pi + 1;
+            const int k1 = i1 / G::NC8, c1 = i1 % G::NC8;
+            const uint32_t a1 = a_item(k1, c1), b1 = b_item(k1, c1);
+            uint32_t a2, b2;
+            if (i2 < G::NX) {
+              a2 = a_item(i2 / G::NC8, i2 % G::NC8);
+              b2 = b_item(i2 / G::NC8, i2 % G::NC8);
+            } else {  // odd count: the second half meets the zero half-strips
+              a2 = a1 + 1;
+              b2 = b_item(5, 0);
             }
-            tc_mma_lo<1>(dcol, ao + 1 * (G::PLANE_BYTES / 16), a_hi,
-                         b_lo + (uint32_t)(((1 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
-            tc_mma_lo<1>(dcol, ao + 2 * (G::PLANE_BYTES / 16), a_hi,
-                         b_lo + (uint32_t)(((2 * G::KC + kc) * 2 * G::GB + bstrip) * 16), b_hi, idesc);
+            const uint32_t alo = a_lo + arow + a1 + ((a2 - a1) << 16);
+            const uint32_t blo = b_lo + b1 + bsh + ((b2 - b1) << 16);
+            if (rho == 0 && pi == 0)
+              tc_mma_lo<0>(dcol, alo, a_hi, blo, b_hi, idesc);
+            else
+              tc_mma_lo<1>(dcol, alo, a_hi, blo, b_hi, idesc);
+          }
+#pragma unroll
+          for (int c = 0; c < G::NC8; ++c) {  // square items (hi, lo) into S
+            const uint32_t a1 = a_item(3, c), a2 = a_item(4, c);
+            const uint32_t b1 = b_item(3, c), b2 = b_item(4, c);
+            const uint32_t alo = a_lo + arow + a1 + ((a2 - a1) << 16);
+            const uint32_t blo = b_lo + b1 + bsh + ((b2 - b1) << 16);
+            if (rho == 0 && c == 0)
+              tc_mma_lo<0>(dcol + G::N, alo, a_hi, blo, b_hi, idesc);
+            else
+              tc_mma_lo<1>(dcol + G::N, alo, a_hi, blo, b_hi, idesc);
           }
         }
         tc_commit(mma_bar + (i & 1));
@@ -390,20 +415,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_search_tc(ImgState s, int nx,
       for (int kk = 0; kk < KPW; ++kk) {
         const int k = kh + 4 * kk;
         if (k >= G::RP) break;  // warp-uniform
-        uint32_t X[8], Hv[8], Lv[8];
+        uint32_t X[8], Sv[8];
         const uint32_t ta = tmem + ((uint32_t)(32 * wq) << 16) + buf + (uint32_t)(8 * k);
         tc_ld8(ta, X);
-        tc_ld8(ta + G::N, Hv);
-        tc_ld8(ta + 2 * G::N, Lv);
+        tc_ld8(ta + G::N, Sv);
         tc_wait_ld();
         const int qy = t.y0 + 2 * k + a_row + R;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
           const int qx = t.x0 + 8 * a_blk + b + R;
           const int xv = __float2int_rn(__uint_as_float(X[b]));
-          const int hv = __float2int_rn(__uint_as_float(Hv[b]));
-          const int lv = __float2int_rn(__uint_as_float(Lv[b]));
-          const uint32_t ssd = (uint32_t)(a2 - 2 * xv + 256 * hv + lv);
+          const int sv = __float2int_rn(__uint_as_float(Sv[b]));
+          const uint32_t ssd = (uint32_t)(a2 - 2 * xv + sv);
           const unsigned long long key = ((unsigned long long)ssd << 32) | (unsigned)(qy * s.W + qx);
           if (cnt[kk][b] == 0 && key < best) best = key;
         }
