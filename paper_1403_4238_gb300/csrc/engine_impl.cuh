@@ -302,11 +302,13 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   // Roles: CTAs [0, ns) search, batch b going to CTA b mod ns (batches cost
   // alike).  The last CTA of the team is the leader: it runs the speculative
   // phase of each iteration while the others search, waits for their keys,
-  // applies the update and publishes the next round; it searches only in a
-  // team of one.  A CTA that neither searches nor leads idles until the image
-  // is done.
-  const bool lead_searches = tsize == 1;
-  const int ns = lead_searches ? 1 : min(tsize - 1, nbatch);
+  // applies the update and publishes the next round.  When the image has
+  // many batches per CTA (small teams in the batched form) the leader also
+  // searches its share after the speculative phase, which is short next to
+  // a CTA's share of such a search.  A CTA that neither searches nor leads
+  // idles until the image is done.
+  const bool lead_searches = tsize == 1 || nbatch >= 8 * tsize;
+  const int ns = lead_searches ? tsize : min(tsize - 1, nbatch);
   const bool leader = rank == tsize - 1;
   const bool searcher = rank < ns;
   const unsigned n_wait = (unsigned)(lead_searches ? ns - 1 : ns);
