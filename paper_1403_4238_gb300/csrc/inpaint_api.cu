@@ -19,6 +19,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -803,24 +804,18 @@ void plan_teams(const std::vector<double>& work, int grid, std::vector<int>& tea
     }
     return;
   }
-  double total = 0.0;
-  for (double w : work) total += w;
-  const int extra = grid - n;
+  // one CTA per image, then each further CTA to the team whose work per CTA
+  // is largest (minimises the largest work per CTA, i.e. the batch's end)
   team_size.assign(n, 1);
   team_imgs.assign(n, {});
-  std::vector<std::pair<double, int>> rem;
-  int used = 0;
-  for (int i = 0; i < n; ++i) {
-    const double share = total > 0 ? extra * work[i] / total : (double)extra / n;
-    const int k = (int)share;
-    team_size[i] += k;
-    used += k;
-    rem.emplace_back(share - k, i);
+  std::priority_queue<std::pair<double, int>> pq;
+  for (int i = 0; i < n; ++i) pq.emplace(work[i], i);
+  for (int k = 0; k < grid - n; ++k) {
+    const int i = pq.top().second;
+    pq.pop();
+    team_size[i] += 1;
+    pq.emplace(work[i] / team_size[i], i);
   }
-  std::sort(rem.begin(), rem.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
-    return a.first > b.first;
-  });
-  for (int k = 0; k < extra - used; ++k) team_size[rem[k % n].second] += 1;
   for (int i = 0; i < n; ++i) {
     img_team[i] = i;
     team_imgs[i].push_back(i);

@@ -79,11 +79,10 @@ struct Ctrl {
 constexpr int kSpecOutside = -2;   // window pixel outside the image
 constexpr int kSpecNotFront = -1;  // in the image, not on the post-fill front
 
-// Thread that handles entry k of a compact work list: consecutive entries go
+// Entry of a compact work list handled by thread t: consecutive entries go
 // to warps 0..3 in turn (one warp per SM sub-partition), so a short list of
 // long FP64 dependency chains uses all four sub-partitions with few active
 // lanes each.
-__device__ inline int list_thread(int k) { return ((k & 3) << 5) | ((k >> 2) & 31) | ((k >> 7) << 7); }
 __device__ inline int list_entry(int t) { return ((t & 31) << 2) | ((t >> 5) & 3) | ((t >> 7) << 7); }
 
 // Data-term table: D = (dot / sqrt(nn)) / 510 for every |n|^2 = nn a Sobel
