@@ -175,6 +175,11 @@ def l2_flush(buf):
 # per clock.
 EVALS_PER_CLK_SM = 64
 
+# DRAM bytes (read + write) of one k_engine launch on the headline workload,
+# from an ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum: 2.332 MB + 1.827 MB); None once the kernel changes.
+ENGINE_TRAFFIC_BYTES = 4159488
+
 
 def measured_peaks():
     try:
@@ -265,7 +270,7 @@ def batch_section(api, flush, steps, log):
     cases = synth.batch_cases(64)
     tf = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
                       "tuning_bench.txt")
-    table = autotune.tune((4, 5), autotune.BUCKETS[:3], iters=32, log=lambda *a: None)
+    table = autotune.tune((4, 5), log=lambda *a: None)
     autotune.write(table, tf)
     items = [(c.rgb, c.mask, c.r) for c in cases]
     with api.Batch(items, tuning_file=tf) as b:
@@ -297,7 +302,7 @@ def batch_section(api, flush, steps, log):
     return {"images": len(cases), "images_per_s": len(cases) / (bms / 1e3), "ms_per_batch": bms,
             "ms_sequential": seq_ms, "speedup_vs_sequential": seq_ms / bms, "identical_outputs": bool(same),
             "teams": plan["teams"], "grid": plan["grid"], "graph": "reset and run captured in CUDA graphs",
-            "autotune": [{"r": r, "max_pixels": mp, "rows": rows} for r, mp, rows, _ in table]}
+            "autotune": [{"r": r, "max_pixels_per_cta": mp, "rows": rows} for r, mp, rows, _ in table]}
 
 
 def serving_section(api, n_req, pool_n=24):
@@ -430,7 +435,8 @@ def main():
                     "h2d_bytes_per_step": 4 * W * H, "d2h_bytes_per_step": 3 * W * H},
             "gpu_launches": (launches_init(H) + 1) * args.steps,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "evals/s", "frac": ach / peak,
-                         "traffic": None, "kernel": "k_engine (one persistent launch per removal)",
+                         "traffic": ENGINE_TRAFFIC_BYTES, "traffic_unit": "bytes per launch (ncu)",
+                         "kernel": "k_engine (one persistent launch per removal)",
                          "peak_source": f"{sms} SMs x {EVALS_PER_CLK_SM} evals/clk x {mhz:.0f} MHz",
                          "search_phase": {"ns": search_ns, "iters": timed_iters,
                                           "evals_per_s": evals_per_removal / (search_ns * 1e-9) if search_ns else None},

@@ -88,7 +88,8 @@ typedef struct {
                             1 or 2; 0 = chosen by the library */
   const char* tuning_file; /* NULL, or a text table written by the autotuner: one line
                             "radius max_pixels rows_per_warp" per bucket; the first
-                            line with the image's radius and W*H <= max_pixels
+                            line with the image's radius and max_pixels >= the image's
+                            pixels per CTA of its team (W*H / CTAs working on it)
                             gives rows_per_warp when tile_rows is 0 */
 } inpaint_options;
 
@@ -220,10 +221,11 @@ int inpaint_best_patch_noalloc(const uint8_t* d_rgb, const uint8_t* d_mask, int 
 /* ---- Batched form: many independent images in one persistent launch ----
  * Every image runs the same fill loop as inpaint_run, bit for bit; the CTAs
  * of one cooperative launch are split into teams, each team running the loop
- * of its images one after the other (team sizes proportional to each image's
- * estimated work; images of any radius 1..8 mix in one launch).  Search
- * batch heights come from the tuning table (see inpaint_autotune in the
- * Python package) when opt->tuning_file names one, else from a size rule. */
+ * of its images one after the other (team sizes chosen to even out each image's
+ * estimated work per CTA; images of any radius 1..8 mix in one launch).  Search
+ * batch heights come from the tuning table (written by the autotune module
+ * of the Python package) when opt->tuning_file names one, else from a rule
+ * on the batches per CTA. */
 typedef struct {
   const uint8_t* rgb;   /* host, H rows of rgb_stride_bytes, 3 bytes per pixel */
   int width, height, rgb_stride_bytes;

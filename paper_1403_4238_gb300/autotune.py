@@ -1,11 +1,15 @@
 """Autotuner for the engine's search batch shape.
 
-The persistent engine stages search batches of 16 warps x rows x 128
-candidate columns; rows per warp (1 or 2) trades staging reuse against how
-many batches each CTA gets.  For each (patch radius, image-size bucket) this
-times a bounded prefix of a synthetic removal with both shapes on the GPU at
-hand and writes the winner to a tuning file, one line per bucket:
-"radius max_pixels rows_per_warp".  The library reads it through
+A search batch is 16 warps x rows x 128 candidate columns; with 1 row per
+warp each lane keeps 4 candidates of one row, with 2 rows the half-warps
+take two rows and each lane 8 candidates (cheaper per evaluation, but
+batches twice as large, so fewer of them to spread over a team's CTAs).
+Which is faster depends on how many pixels each CTA of a team works on, so
+the table is keyed by radius and pixels per CTA, and measured in the batched
+form itself: n copies of one synthetic image share the GPU's CTAs (teams of
+about SMs / n CTAs), for several n, each shape timed over a bounded number
+of iterations.  The table is a text file, one line per bucket:
+"radius max_pixels_per_cta rows_per_warp"; the library reads it through
 inpaint_options.tuning_file (single images, batches and the server).
 
     python -m paper_1403_4238_gb300.autotune --out tuning.txt --radii 4,5
@@ -16,47 +20,54 @@ import argparse
 import math
 import time
 
-import numpy as np
-
 from . import api, synth
 
-# pixel-count buckets and a representative 16:9-ish size for each
-BUCKETS = [(160_000, (480, 320)), (400_000, (768, 512)), (1_000_000, (1280, 720)),
-           (2_500_000, (1920, 1080)), (1 << 30, (2560, 1440))]
+IMAGE = (480, 320)          # tuning image size
+COPIES = (1, 9, 38, 152)    # images per launch (scaled to the SM count)
+ITERS = 24                  # iterations timed per run
 
 
-def time_shape(case, rows, iters, reps=3):
-    """Evaluations per second of `iters` engine iterations of the case."""
+def _rate(cases, rows, iters, reps=2):
+    """Evaluations per second of `iters` iterations of every image of a batch."""
     import torch
 
     best = math.inf
     evals = 0
-    with api.Inpainter(case.rgb, case.mask, case.r, loop="engine", tile_rows=rows) as ip:
-        drgb = torch.from_numpy(case.rgb).cuda()
-        dmask = torch.from_numpy(case.mask).cuda()
-        torch.cuda.synchronize()
+    with api.Batch(cases, tile_rows=rows) as b:
         for _ in range(reps):
-            ip.reset(drgb, dmask)
+            b.reset()
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ip.run(max_iters=iters)
-            dt = time.perf_counter() - t0
-            best = min(best, dt)
-            evals = ip.info()["evals"]
+            b.run(max_iters=iters)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        evals = sum(b.result(i)[2] for i in range(len(cases)))
     return evals / best
 
 
-def tune(radii, buckets=BUCKETS, iters=48, seed=9, log=print):
-    """Returns [(radius, max_pixels, rows_per_warp, {rows: evals/s})]."""
+def tune(radii, iters=ITERS, seed=9, log=print):
+    """Returns [(radius, max_pixels_per_cta, rows_per_warp, {rows: evals/s})]."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    W, H = IMAGE
+    base = [synth.Case(f"tune{k}", synth.image(W, H, 12, 30.0, seed + k),
+                       synth.ellipse_mask(W, H, 3, 0.05, 0.06, seed + 100 + k), 4) for k in range(4)]
     table = []
     for r in radii:
-        for max_px, (W, H) in buckets:
-            case = synth.Case(f"tune_{W}x{H}_r{r}", synth.image(W, H, 12, 30.0, seed),
-                              synth.ellipse_mask(W, H, 3, 0.05, 0.06, seed + 1), r)
-            rates = {rows: time_shape(case, rows, iters) for rows in (1, 2)}
-            best = max(rates, key=rates.get)
-            table.append((r, max_px, best, rates))
-            log(f"r={r} <= {max_px} px ({W}x{H}): " +
-                ", ".join(f"rows {k}: {v:.3e} evals/s" for k, v in rates.items()) + f" -> {best}")
+        points = []
+        for c in COPIES:
+            n = max(1, min(sms, round(c * sms / 152)))
+            cases = [(base[i % 4].rgb, base[i % 4].mask, r) for i in range(n)]
+            per_cta = W * H * n / sms
+            rates = {rows: _rate(cases, rows, iters) for rows in (1, 2)}
+            points.append((per_cta, max(rates, key=rates.get), rates))
+            log(f"r={r} images={n} ({per_cta:.0f} px per CTA): " +
+                ", ".join(f"rows {k}: {v:.3e} evals/s" for k, v in rates.items()))
+        points.sort()
+        for k, (px, rows, rates) in enumerate(points):
+            bound = math.sqrt(px * points[k + 1][0]) if k + 1 < len(points) else float(1 << 40)
+            table.append((r, int(bound), rows, rates))
     return table
 
 
@@ -70,12 +81,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--radii", default="4,5")
-    ap.add_argument("--iters", type=int, default=48)
-    ap.add_argument("--max-pixels", type=int, default=2_500_000)
+    ap.add_argument("--iters", type=int, default=ITERS)
     args = ap.parse_args()
     radii = [int(x) for x in args.radii.split(",")]
-    buckets = [b for b in BUCKETS if b[0] <= args.max_pixels] or BUCKETS[:1]
-    write(tune(radii, buckets, args.iters), args.out)
+    write(tune(radii, args.iters), args.out)
 
 
 if __name__ == "__main__":

@@ -194,7 +194,8 @@ bool use_engine(const inpaint_ctx* c) {
 }
 
 // Rows per warp from an autotuner table: lines "radius max_pixels rows";
-// the first line with this radius and max_pixels >= W*H wins; 0 if none.
+// the first line with this radius and max_pixels >= `pixels` (the image's
+// pixels per CTA of its team) wins; 0 if none.
 int tuned_rows_per_warp(const char* path, int r, long long pixels) {
   if (!path) return 0;
   FILE* f = fopen(path, "r");
@@ -238,7 +239,7 @@ int setup_engine(inpaint_ctx* c) {
     return INPAINT_ERR_UNSUPPORTED;
   }
   const int grid = sms * bps;
-  if (!sr) sr = tuned_rows_per_warp(c->opt.tuning_file, c->r, (long long)c->W * c->H);
+  if (!sr) sr = tuned_rows_per_warp(c->opt.tuning_file, c->r, (long long)c->W * c->H / grid);
   if (!sr) sr = pick_rows_per_warp(c->st, grid);
   c->eng_smem = f->smem_bytes(sr);
   CK(engine_occupancy(c->eng_smem, &bps));
@@ -852,8 +853,9 @@ int engine_set_prepare(EngineSet& es, const std::vector<inpaint_ctx*>& cs, const
   for (int i = 0; i < n; ++i) {
     inpaint_ctx* c = cs[i];
     int sr = opt.tile_rows;
-    if (!sr) sr = tuned_rows_per_warp(opt.tuning_file, c->r, (long long)c->W * c->H);
-    if (!sr) sr = pick_rows_per_warp(c->st, es.team_size[es.img_team[i]]);
+    const int tsz = es.team_size[es.img_team[i]];
+    if (!sr) sr = tuned_rows_per_warp(opt.tuning_file, c->r, (long long)c->W * c->H / tsz);
+    if (!sr) sr = pick_rows_per_warp(c->st, tsz);
     c->st.srw = sr;
     imgs[i] = c->st;
     if (make_image_tmap(c->st, sr, &maps[2 * (size_t)i]) != 0) {

@@ -91,3 +91,30 @@ def test_batch_iteration_limit_and_resume(api):
         for i in range(len(cases)):
             out, iters, _ = b.result(i)
             assert iters == refs[i].iters and np.array_equal(out, refs[i].rgb)
+
+
+def test_batch_small_teams_with_searching_leaders(api):
+    # 40 images on the GPU's CTAs: teams of a few CTAs, each with many search
+    # batches, so the team leader searches its share besides the update
+    rng = np.random.default_rng(21)
+    cases = []
+    for i in range(40):
+        W, H = int(rng.integers(360, 480)), int(rng.integers(260, 340))
+        s = int(rng.integers(0, 2**31))
+        cases.append((synth.image(W, H, 8, 30.0, s), synth.ellipse_mask(W, H, 2, 0.01, 0.02, s + 1), 4))
+    with api.Batch(cases) as b:
+        plan = b.plan()
+        assert plan["teams"] == 40 and max(plan["team_size"]) >= 2
+        st = b.run()
+        assert all(x == 0 for x in st), st
+        outs = [b.result(i) for i in range(len(cases))]
+    for i, (rgb, mask, r) in enumerate(cases):
+        if i % 5:
+            continue  # every fifth image against a single-image run, two against the oracle
+        with api.Inpainter(rgb, mask, r) as ip:
+            ip.run()
+            assert np.array_equal(outs[i][0], ip.result()), i
+            assert outs[i][2] == ip.info()["evals"], i
+        if i in (0, 20):
+            ref = oracle.run(rgb, mask, r)
+            assert np.array_equal(outs[i][0], ref.rgb) and outs[i][1] == ref.iters, i
