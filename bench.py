@@ -317,7 +317,7 @@ def serving_section(api, n_req, pool_n=24):
         with api.Inpainter(c.rgb, c.mask, c.r) as ip:
             ip.run()
             alone.append(ip.result())
-    with api.Server(hbm_budget_bytes=40 << 30, max_slots=256, iters_per_tick=64) as srv:
+    with api.Server(hbm_budget_bytes=40 << 30, max_slots=256, iters_per_tick=0) as srv:
         ids = []
         t0 = time.perf_counter()
         for i, t in enumerate(trace):

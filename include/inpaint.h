@@ -274,8 +274,10 @@ void inpaint_batch_destroy(inpaint_batch* b);
  * while slots are free and the estimated device memory of the admitted ones
  * stays within the budget (their state stays on the device until they
  * finish); each tick is one persistent engine launch over every active slot
- * (up to iters_per_tick iterations each), after which finished requests
- * release their memory and their result waits for inpaint_server_poll.
+ * that runs until about 20 ms of device time have passed (teams stop between
+ * iterations and resume in the next tick) or each slot has done
+ * iters_per_tick iterations, after which finished requests release their
+ * memory and their result waits for inpaint_server_poll.
  * A request's result does not depend on what else is in flight: it equals
  * inpaint_run on that image alone. */
 #define INPAINT_PENDING 2   /* inpaint_server_poll: request not finished yet */
@@ -298,8 +300,9 @@ typedef struct {
 } inpaint_server_stats;
 
 /* hbm_budget_bytes: limit on the estimated device memory of active requests;
- * max_slots: limit on simultaneously active requests; iters_per_tick: engine
- * iterations per slot per tick (<= 0: 64).  opt as for inpaint_create
+ * max_slots: limit on simultaneously active requests; iters_per_tick: at most
+ * this many engine iterations per slot per tick (<= 0: no limit besides the
+ * tick's time budget).  opt as for inpaint_create
  * (cuda_stream ignored: the server makes its own). */
 int inpaint_server_create(size_t hbm_budget_bytes, int max_slots, int iters_per_tick,
                           const inpaint_options* opt, inpaint_server** out);

@@ -316,7 +316,7 @@ class Server:
     poll(id) returns None while pending, else (rgb, info dict).
     """
 
-    def __init__(self, hbm_budget_bytes: int = 40 << 30, max_slots: int = 256, iters_per_tick: int = 64,
+    def __init__(self, hbm_budget_bytes: int = 40 << 30, max_slots: int = 256, iters_per_tick: int = 0,
                  *, tile_rows: int = 0, tuning_file: str | None = None):
         torch = _torch()
         self.lib = _lib.load()

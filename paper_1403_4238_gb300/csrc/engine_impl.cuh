@@ -457,14 +457,25 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
         t_b = globaltimer();
         ok = update_phase<R>(s, tpart, ns, usm, uca);  // ends with a __syncthreads
         if (ok) {
-          // the next target is known: publish it before the bookkeeping
-          stop = usm.remaining <= 0 || usm.next_key == 0ull || usm.it + 1 >= __ldcg(&c->iter_limit) ||
-                 __ldcg(&c->status) != 0 || __ldcg(ea.err) != 0;
+          // the next target is known: publish it before the bookkeeping.
+          // Thread 0 decides (the inputs are global and may change under
+          // other threads' feet) and the barrier below shares the decision.
+          if (tid == 0) {
+            bool st = usm.remaining <= 0 || usm.next_key == 0ull ||
+                      usm.it + 1 >= __ldcg(&c->iter_limit) || __ldcg(&c->status) != 0 ||
+                      __ldcg(ea.err) != 0;
+            if (!st && ea.tick_ns && globaltimer() - x.t_start > ea.tick_ns) {
+              st = true;  // the launch's time budget is spent: resume in the next launch
+              tc->expired = 1u;
+            }
+            tl.stop = st;
+          }
           npx = usm.next_idx % s.W;
           npy = usm.next_idx / s.W;
         }
       }
       __syncthreads();
+      stop = ok ? tl.stop != 0 : true;
       if (tid == 0) {
         tc->arrive = 0u;
         st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));

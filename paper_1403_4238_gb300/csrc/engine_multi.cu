@@ -50,8 +50,15 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
   x.ph0 = 0;
   x.ph1 = 0;
   x.epoch = (unsigned)ld_acquire64_pub(&x.tc->pub);
-  for (int li = ea.team_img_off[team]; li < ea.team_img_off[team + 1]; ++li)
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(x.t_start));
+  for (int li = ea.team_img_off[team]; li < ea.team_img_off[team + 1]; ++li) {
     run_by_radius(ea, ea.team_img[li], x);
+    // the leader's last publication of the image was acquired by every CTA
+    // of the team, so all of them see the same flag here
+    unsigned expired;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(expired) : "l"(&x.tc->expired) : "memory");
+    if (expired) break;
+  }
 }
 
 cudaError_t engine_occupancy(size_t smem, int* blocks_per_sm) {

@@ -930,7 +930,11 @@ int engine_set_prepare(EngineSet& es, const std::vector<inpaint_ctx*>& cs, const
 // has done max_iters more iterations (<= 0: no limit).  Control blocks are
 // read back into es.h_ctrls.  Returns INPAINT_ERR_TIMEOUT if a bounded
 // device wait gave up.
-int engine_set_run(EngineSet& es, const std::vector<inpaint_ctx*>& cs, int max_iters, cudaStream_t st) {
+// Runs every member until it is done, or for at most max_iters (> 0) more
+// iterations, or until the launch has run tick_ns (> 0; teams stop between
+// iterations and resume in the next call).
+int engine_set_run(EngineSet& es, const std::vector<inpaint_ctx*>& cs, int max_iters, cudaStream_t st,
+                   unsigned long long tick_ns = 0ull) {
   const int n = (int)cs.size();
   for (int i = 0; i < n; ++i)
     CK(cudaMemcpyAsync(es.h_ctrls + i, cs[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -945,7 +949,9 @@ int engine_set_run(EngineSet& es, const std::vector<inpaint_ctx*>& cs, int max_i
   }
   CK(cudaMemsetAsync((void*)es.ea.teams, 0, sizeof(TeamCtl) * es.n_teams, st));
   CK(cudaMemsetAsync(es.d_err, 0, sizeof(int), st));
+  es.ea.tick_ns = tick_ns;
   CK(engine_launch(es.smem, es.ea, es.grid, st));
+  es.ea.tick_ns = 0ull;
   CK(cudaMemcpyAsync(es.h_pinned, es.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   for (int i = 0; i < n; ++i)
     CK(cudaMemcpyAsync(es.h_ctrls + i, cs[i]->st.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -1262,6 +1268,11 @@ size_t est_bytes(int W, int H, int n_omega) {
 
 }  // namespace
 
+// Device time budget of one serving tick: long enough to amortise the
+// launch and the host's admission work, short enough to admit new requests
+// often.
+constexpr unsigned long long kServerTickNs = 20000000ull;
+
 struct inpaint_server {
   size_t budget = 0, used = 0;
   int max_slots = 0, iters_per_tick = 64, device = 0;
@@ -1363,7 +1374,7 @@ struct inpaint_server {
           work.push_back(work_of(*q->ctx->h_ctrl));
         }
         int rc = engine_set_prepare(es, cs, work, opt, da, stream);
-        if (rc >= 0) rc = engine_set_run(es, cs, iters_per_tick, stream);
+        if (rc >= 0) rc = engine_set_run(es, cs, iters_per_tick, stream, kServerTickNs);
         for (size_t i = 0; i < act.size(); ++i) {
           const Ctrl& h = rc >= 0 ? es.h_ctrls[i] : *act[i]->ctx->h_ctrl;
           *act[i]->ctx->h_ctrl = h;  // mirror for the next work estimate
@@ -1404,7 +1415,7 @@ int inpaint_server_create(size_t hbm_budget_bytes, int max_slots, int iters_per_
   s->opt.form = INPAINT_FORM_PLAIN;
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
-  s->iters_per_tick = iters_per_tick > 0 ? iters_per_tick : 64;
+  s->iters_per_tick = iters_per_tick > 0 ? iters_per_tick : 0;
   if (cudaGetDevice(&s->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete s;

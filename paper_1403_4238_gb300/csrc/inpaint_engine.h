@@ -15,7 +15,8 @@ constexpr int kEngCountW = 132;  // count words staged per batch row (128 + alig
 struct TeamCtl {
   unsigned long long pub;  // epoch | next px | next py | stop (release-published)
   unsigned arrive;         // searchers arrived in the current iteration
-  unsigned pad[29];        // keep teams on separate 128-byte lines
+  unsigned expired;        // the launch's time budget ended this team's work
+  unsigned pad[28];        // keep teams on separate 128-byte lines
 };
 
 struct EngineArgs {
@@ -29,6 +30,8 @@ struct EngineArgs {
   unsigned long long* partials;// [grid]
   int* err;                    // INPAINT_ERR_TIMEOUT if a bounded wait gave up
   unsigned long long wait_limit_ns;
+  unsigned long long tick_ns;  // > 0: teams stop between iterations once the launch
+                               // has run this long (serving ticks); 0: run to the end
 };
 
 // Per-CTA engine state carried from one image of a team's list to the next.
@@ -39,6 +42,7 @@ struct EngCtx {
   unsigned long long* tpart;    // partial keys of the team's CTAs
   uint32_t ph0, ph1;            // phase parities of the two TMA barriers
   unsigned epoch;               // team publications seen
+  unsigned long long t_start;   // global timer at the CTA's start (tick budget)
 };
 
 // Per-image engine body for radius R and SRW rows per warp (engine_r<R>.cu),

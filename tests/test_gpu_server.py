@@ -87,3 +87,20 @@ def test_poll_pending_and_unknown(api):
             out, info = srv.poll(rid)
             assert info["status"] == 0
         assert srv.lib.inpaint_server_poll(srv.s, 987654, None, 0, None) == -1  # unknown id
+
+
+def test_time_budget_ticks_resume_long_requests(api):
+    # a 1920x1080 removal takes several 20 ms ticks: its team stops between
+    # iterations when the tick's device time is spent and resumes in the
+    # next launch, beside short requests that finish within one tick
+    big = synth.hd_blob()
+    reqs = [(big.rgb, big.mask, big.r)] + requests(5, 11)
+    with api.Server(hbm_budget_bytes=8 << 30, max_slots=16, iters_per_tick=0) as srv:
+        ids = [srv.submit(*q) for q in reqs]
+        srv.wait_idle(300)
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["ticks"] >= 3
+        for rid, q in zip(ids, reqs):
+            out, info = srv.poll(rid)
+            assert info["status"] == 0
+            assert np.array_equal(out, alone(api, *q))
