@@ -111,6 +111,20 @@ __device__ inline void compute_rows(const uint32_t* __restrict__ stage, int row0
 // each lane eight adjacent candidates (columns (lane & 15) * 8 ...), so both
 // half-warps use the same target row at a time: the row-mask branch stays
 // warp-uniform and costs half as much per evaluation as with four candidates.
+// SSD terms of target columns dx in [D0, D0 + L) for eight candidates, no
+// per-column test (a contiguous run of known target pixels).
+template <int R, int D0, int L, int TP, int N8>
+__device__ __forceinline__ void ssd_run8(const uint32_t (&t)[TP], const uint32_t (&r)[N8],
+                                         uint32_t (&acc)[8]) {
+#pragma unroll
+  for (int dx = D0; dx < D0 + L; ++dx)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
+      acc[k] = __dp4a(d, d, acc[k]);
+    }
+}
+
 template <int R>
 __device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row, int col,
                                      const uint32_t* __restrict__ tgt,
@@ -144,14 +158,27 @@ __device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row
       t[4 * i + 2] = v.z;
       t[4 * i + 3] = v.w;
     }
+    const uint32_t um = ~m & G::FULL;  // unknown columns of the row
     if (m == G::FULL) {
-#pragma unroll
-      for (int dx = 0; dx < P; ++dx) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
-          acc[k] = __dp4a(d, d, acc[k]);
-        }
+      ssd_run8<R, 0, P>(t, r, acc);
+    } else if ((m & (m + 1)) == 0 || (um & (um + 1)) == 0) {
+      // the known columns are one run at the start or at the end of the row
+      // (the usual shape next to the fill front): straight-line code
+      const bool at_end = (m & 1u) == 0;
+      switch (__popc(m)) {
+#define INP_RUN8(n)                                             \
+  case n:                                                       \
+    if constexpr (n < P) {                                      \
+      if (at_end) ssd_run8<R, P - n, n>(t, r, acc);             \
+      else ssd_run8<R, 0, n>(t, r, acc);                        \
+    }                                                           \
+    break;
+        INP_RUN8(1) INP_RUN8(2) INP_RUN8(3) INP_RUN8(4) INP_RUN8(5) INP_RUN8(6) INP_RUN8(7)
+        INP_RUN8(8) INP_RUN8(9) INP_RUN8(10) INP_RUN8(11) INP_RUN8(12) INP_RUN8(13) INP_RUN8(14)
+        INP_RUN8(15) INP_RUN8(16)
+#undef INP_RUN8
+        default:
+          break;
       }
     } else {
 #pragma unroll
