@@ -115,13 +115,15 @@ __device__ inline void compute_rows(const uint32_t* __restrict__ stage, int row0
 // per-column test (a contiguous run of known target pixels).
 template <int R, int D0, int L, int TP, int N8>
 __device__ __forceinline__ void ssd_run8(const uint32_t (&t)[TP], const uint32_t (&r)[N8],
-                                         uint32_t (&acc)[8]) {
+                                         uint32_t (&acc)[16]) {
+  // even and odd columns go to separate accumulators: twice the independent
+  // dot-product chains per lane
 #pragma unroll
   for (int dx = D0; dx < D0 + L; ++dx)
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
-      acc[k] = __dp4a(d, d, acc[k]);
+      acc[(dx & 1) * 8 + k] = __dp4a(d, d, acc[(dx & 1) * 8 + k]);
     }
 }
 
@@ -132,8 +134,9 @@ __device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row
   using G = EngGeom<R, 2>;
   constexpr int P = G::P, BW = G::BW, N8 = (8 + P - 1 + 3) & ~3;
   static_assert(15 * 8 + N8 <= BW, "row strip must stay inside the tile");
+  uint32_t acc2[16];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) acc[k] = 0;
+  for (int k = 0; k < 16; ++k) acc2[k] = 0;
 #pragma unroll 1
   for (int dy = 0; dy < P; ++dy) {
     const uint32_t m = rowmask[dy];
@@ -160,7 +163,7 @@ __device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row
     }
     const uint32_t um = ~m & G::FULL;  // unknown columns of the row
     if (m == G::FULL) {
-      ssd_run8<R, 0, P>(t, r, acc);
+      ssd_run8<R, 0, P>(t, r, acc2);
     } else if ((m & (m + 1)) == 0 || (um & (um + 1)) == 0) {
       // the known columns are one run at the start or at the end of the row
       // (the usual shape next to the fill front): straight-line code
@@ -169,8 +172,8 @@ __device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row
 #define INP_RUN8(n)                                             \
   case n:                                                       \
     if constexpr (n < P) {                                      \
-      if (at_end) ssd_run8<R, P - n, n>(t, r, acc);             \
-      else ssd_run8<R, 0, n>(t, r, acc);                        \
+      if (at_end) ssd_run8<R, P - n, n>(t, r, acc2);            \
+      else ssd_run8<R, 0, n>(t, r, acc2);                       \
     }                                                           \
     break;
         INP_RUN8(1) INP_RUN8(2) INP_RUN8(3) INP_RUN8(4) INP_RUN8(5) INP_RUN8(6) INP_RUN8(7)
@@ -187,12 +190,14 @@ __device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
-            acc[k] = __dp4a(d, d, acc[k]);
+            acc2[(dx & 1) * 8 + k] = __dp4a(d, d, acc2[(dx & 1) * 8 + k]);
           }
         }
       }
     }
   }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = acc2[k] + acc2[8 + k];
 }
 
 // ---------------------------------------------------------------- kernel
