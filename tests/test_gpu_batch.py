@@ -118,3 +118,24 @@ def test_batch_small_teams_with_searching_leaders(api):
         if i in (0, 20):
             ref = oracle.run(rgb, mask, r)
             assert np.array_equal(outs[i][0], ref.rgb) and outs[i][1] == ref.iters, i
+
+
+def test_batch_more_images_than_ctas_mixed_radii(api):
+    # more images than CTAs, radii 1..8 mixed: single-CTA teams, some running
+    # two images in turn
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    n = sms + 12
+    cases = mixed_cases(n, 33, wmax=72, hmax=60)
+    with api.Batch(cases) as b:
+        plan = b.plan()
+        assert plan["teams"] == plan["grid"] and max(plan["team_size"]) == 1
+        st = b.run()
+        assert all(x in (0, 1) for x in st), st
+        for i in range(0, n, 17):
+            rgb, mask, r = cases[i]
+            ref = oracle.run(rgb, mask, r)
+            out, iters, evals = b.result(i)
+            assert iters == ref.iters and evals == ref.evals
+            assert np.array_equal(out, ref.rgb), i
