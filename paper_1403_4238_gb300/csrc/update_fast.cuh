@@ -481,8 +481,40 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const int ny_in = min(py + R, H - 1) - max(py - R, 0) + 1;
   const int n_known = nx_in * ny_in - filled;
 
-  // isophotes of the new grey levels
+  // isophotes of the new grey levels, then for every window pixel the
+  // strongest one of its patch (first in row-major order on ties) as a
+  // separable windowed maximum of keys (|grad|^2 + 1) << 12 | (4095 - l) over
+  // local indices l; the confidence array is free here and holds the keys
   stage_isophotes<R>(sm);
+  __syncthreads();
+  constexpr int HR = NW + 2 * R;  // rows of the horizontal pass
+  uint32_t* hkey = reinterpret_cast<uint32_t*>(sm.cf);
+  uint32_t* wkey = hkey + HR * NW;
+  static_assert(sizeof(sm.cf) >= sizeof(uint32_t) * (HR * NW + NW * NW), "key scratch");
+  static_assert(NS * NS <= 4096, "local index fits in 12 bits");
+  for (int i = tid; i < HR * NW; i += nt) {
+    const int ly = RB - R2 - R + i / NW, lx = RB - R2 + i % NW;
+    uint32_t best = 0u;
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) {
+      const int l = ly * NS + lx + dx;
+      const int m = sm.mag[l];
+      const uint32_t key = m >= 0 ? ((uint32_t)(m + 1) << 12) | (uint32_t)(4095 - l) : 0u;
+      best = key > best ? key : best;
+    }
+    hkey[i] = best;
+  }
+  __syncthreads();
+  for (int i = tid; i < NW * NW; i += nt) {
+    const int wy = i / NW, wx = i % NW;
+    uint32_t best = 0u;
+#pragma unroll
+    for (int dy = 0; dy <= 2 * R; ++dy) {
+      const uint32_t key = hkey[(wy + dy) * NW + wx];
+      best = key > best ? key : best;
+    }
+    wkey[i] = best;
+  }
   __syncthreads();
 
   // priorities of the window (front pixels from the compact list, spread
@@ -502,7 +534,14 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       const int i = sm.list[k];
       const int wx = i % NW - R2, wy = i / NW - R2;
       int gx, gy;
-      isophote_local<R>(sm, RB + wx, RB + wy, &gx, &gy);
+      const uint32_t ik = wkey[i];
+      gx = 0;
+      gy = 0;
+      if (ik) {
+        const int g = sm.gxy[4095 - (int)(ik & 4095u)];
+        gx = (g >> 16) - 512;
+        gy = (g & 0xffff) - 512;
+      }
       const double cc = sm.sC[i];
       const int nrm = sm.snrm[i];
       const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
