@@ -14,6 +14,7 @@
 //   3. the others wait for that epoch (bounded wait, no trap) and go on.
 // No host round trip and no kernel boundary per iteration.
 #pragma once
+#include <type_traits>
 #include <cuda.h>
 
 #include "inpaint_engine.h"
@@ -204,6 +205,7 @@ __device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row
 
 struct EngSmemTail {
   uint64_t full[2];  // TMA completion barriers of the two stages
+  ImgState img;      // the image's state block (a leader that does not search reads it here)
   unsigned long long red64[32];
   int red32[32];
   int flag;
@@ -302,7 +304,18 @@ __device__ inline bool ctrl_active(const Ctrl* c) {
 // Per-image part of the engine: the fill loop of image j for this CTA's
 // team (roles below).  Called by k_engine (engine_multi.cu) through
 // run_image_r<R>_s<SRW>, once per image of the team's list.
+template <int R, int SRW, bool kLeadOnly = false>
+__device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x);
+
+// The loop of a leader that does not search, compiled as a function of its
+// own: none of the search state is live through its phases, so its
+// registers hold the update's working set.
 template <int R, int SRW>
+__device__ __noinline__ void run_lead_only(const EngineArgs& ea, int j, EngCtx& x) {
+  run_image<R, SRW, true>(ea, j, x);
+}
+
+template <int R, int SRW, bool kLeadOnly>
 __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x) {
   using G = EngGeom<R, SRW>;
   constexpr int P = G::P, B = G::B;
@@ -323,7 +336,13 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   uint32_t ph0 = x.ph0, ph1 = x.ph1;
   unsigned epoch = x.epoch;
 
-  const ImgState s = ea.imgs[j];
+  // a leader that does not search reads the image's fields from shared
+  // memory, which keeps about forty registers free for its phases
+  if constexpr (kLeadOnly) {
+    if (tid == 0) tl.img = ea.imgs[j];
+    __syncthreads();
+  }
+  std::conditional_t<kLeadOnly, const ImgState&, const ImgState> s = kLeadOnly ? tl.img : ea.imgs[j];
   const CUtensorMap* map = &ea.tmaps[2 * j];
   const CUtensorMap* cmap = &ea.tmaps[2 * j + 1];
   Ctrl* c = s.ctrl;
@@ -344,6 +363,12 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   const bool leader = rank == tsize - 1;
   const bool searcher = rank < ns;
   const unsigned n_wait = (unsigned)(lead_searches ? ns - 1 : ns);
+  if constexpr (!kLeadOnly) {
+    if (leader && !searcher) {
+      run_lead_only<R, SRW>(ea, j, x);
+      return;
+    }
+  }
   bool resident = false;  // stage0 holds this CTA's only batch of the image
   if (tid == 0) {
     tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
@@ -471,65 +496,77 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     return block_min_u64(best, tl.red64);
   };
 
+  // One iteration of the leader for target (px, py): speculative phase (and
+  // its own search share when it searches), the searchers' keys, update,
+  // publication of the next round, bookkeeping.  Whole block.
+  auto lead_round = [&](int px, int py, bool searches) {
+    const unsigned long long t_a = globaltimer();
+    spec_phase<R>(s, usm, uca, staged);
+    if (searches) {
+      const unsigned long long best = search_round(px, py);
+      if (tid == 0) tpart[rank] = best;
+    }
+    if (tid == 0) tl.flag = wait_arrivals(tc, n_wait, ea.err, limit);
+    __syncthreads();
+    bool stop = true, ok = false;
+    int npx = 0, npy = 0;
+    unsigned long long t_b = 0ull;
+    if (tl.flag) {
+      t_b = globaltimer();
+      ok = update_phase<R>(s, tpart, ns, usm, uca);  // ends with a __syncthreads
+      if (ok) {
+        // the next target is known: publish it before the bookkeeping.
+        // Thread 0 decides (the inputs are global and may change under
+        // other threads' feet) and the barrier below shares the decision.
+        if (tid == 0) {
+          const int lim = __ldcg(&c->iter_limit), status = __ldcg(&c->status), err = __ldcg(ea.err);
+          bool st = usm.remaining <= 0 || usm.next_key == 0ull || usm.it + 1 >= lim || status != 0 ||
+                    err != 0;
+          if (!st && ea.tick_ns && globaltimer() - x.t_start > ea.tick_ns) {
+            st = true;  // the launch's time budget is spent: resume in the next launch
+            tc->expired = 1u;
+          }
+          tl.stop = st;
+        }
+        npx = usm.next_idx % s.W;
+        npy = usm.next_idx / s.W;
+      }
+    }
+    __syncthreads();
+    stop = ok ? tl.stop != 0 : true;
+    if (tid == 0) {
+      tc->arrive = 0u;
+      st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
+      tl.stop = stop;
+      tl.px = npx;
+      tl.py = npy;
+    }
+    staged = ok && !stop;
+    if (staged) stage_nbhd<R, true, true>(s, npx, npy, usm);  // next speculative phase's input
+    if (ok) {
+      update_finish<R>(s, usm);
+      if (tid == 0) {
+        atomicAdd(&c->t_search, t_b - t_a);
+        atomicAdd(&c->t_update, globaltimer() - t_b);
+        atomicAdd(&c->timed_iters, 1);
+      }
+    }
+    ++epoch;
+    prev_px = px;
+    prev_py = py;
+    __syncthreads();
+    if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+  };
+
+  if constexpr (kLeadOnly) {
+    while (!tl.stop) lead_round(tl.px, tl.py, false);
+    x.epoch = epoch;
+    return;
+  }
   while (!tl.stop) {
     const int px = tl.px, py = tl.py;
     if (leader) {
-      const unsigned long long t_a = globaltimer();
-      spec_phase<R>(s, usm, uca, staged);
-      if (searcher) {
-        const unsigned long long best = search_round(px, py);
-        if (tid == 0) tpart[rank] = best;
-      }
-      if (tid == 0) tl.flag = wait_arrivals(tc, n_wait, ea.err, limit);
-      __syncthreads();
-      bool stop = true, ok = false;
-      int npx = 0, npy = 0;
-      unsigned long long t_b = 0ull;
-      if (tl.flag) {
-        t_b = globaltimer();
-        ok = update_phase<R>(s, tpart, ns, usm, uca);  // ends with a __syncthreads
-        if (ok) {
-          // the next target is known: publish it before the bookkeeping.
-          // Thread 0 decides (the inputs are global and may change under
-          // other threads' feet) and the barrier below shares the decision.
-          if (tid == 0) {
-            bool st = usm.remaining <= 0 || usm.next_key == 0ull ||
-                      usm.it + 1 >= __ldcg(&c->iter_limit) || __ldcg(&c->status) != 0 ||
-                      __ldcg(ea.err) != 0;
-            if (!st && ea.tick_ns && globaltimer() - x.t_start > ea.tick_ns) {
-              st = true;  // the launch's time budget is spent: resume in the next launch
-              tc->expired = 1u;
-            }
-            tl.stop = st;
-          }
-          npx = usm.next_idx % s.W;
-          npy = usm.next_idx / s.W;
-        }
-      }
-      __syncthreads();
-      stop = ok ? tl.stop != 0 : true;
-      if (tid == 0) {
-        tc->arrive = 0u;
-        st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
-        tl.stop = stop;
-        tl.px = npx;
-        tl.py = npy;
-      }
-      staged = ok && !stop;
-      if (staged) stage_nbhd<R, true, true>(s, npx, npy, usm);  // next speculative phase's input
-      if (ok) {
-        update_finish<R>(s, usm);
-        if (tid == 0) {
-          c->t_search += t_b - t_a;
-          c->t_update += globaltimer() - t_b;
-          c->timed_iters += 1;
-        }
-      }
-      ++epoch;
-      prev_px = px;
-      prev_py = py;
-      __syncthreads();
-      if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+      lead_round(px, py, true);
       continue;
     }
     if (searcher) {

@@ -369,6 +369,7 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
     stage_nbhd<R, true, true>(s, px, py, sm);
     __syncthreads();
   }
+  if (threadIdx.x == 0) sm.nlist = 0;
   int my = 0;
   for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
     const int l = (RB + i / P - R) * NS + RB + i % P - R;
@@ -383,8 +384,6 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
   }
   const int filled = block_sum_int(my, sm.red32);  // includes __syncthreads
   // post-fill front of the window, compacted
-  if (threadIdx.x == 0) sm.nlist = 0;
-  __syncthreads();
   for (int i = threadIdx.x; i < NW * NW; i += blockDim.x) {
     const int l = (RB + i / NW - R2) * NS + RB + i % NW - R2;
     int nrm = kSpecOutside;
@@ -675,37 +674,41 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
 template <int R>
 __device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm) {
   Ctrl* c = s.ctrl;
+  const bool next = sm.remaining > 0 && sm.next_key != 0ull;
   if (threadIdx.x == 0) {
-    inpaint_step_info* e = &c->last;
-    e->iter = sm.it;
-    e->px = sm.px;
-    e->py = sm.py;
-    e->qx = sm.qx;
-    e->qy = sm.qy;
-    e->ssd = sm.ssd;
-    e->priority = sm.pp;
-    e->confidence = sm.cp;
-    e->filled = sm.n_filled;
-    e->remaining = sm.remaining;
-    e->n_known = sm.n_known;
-    e->n_cand = sm.n_cand;
-    if (sm.it < s.trace_cap) s.trace[sm.it] = *e;
+    // the record is built in registers: no global read-backs on the
+    // leader's critical path
+    inpaint_step_info e;
+    e.iter = sm.it;
+    e.px = sm.px;
+    e.py = sm.py;
+    e.qx = sm.qx;
+    e.qy = sm.qy;
+    e.ssd = sm.ssd;
+    e.priority = sm.pp;
+    e.confidence = sm.cp;
+    e.filled = sm.n_filled;
+    e.remaining = sm.remaining;
+    e.n_known = sm.n_known;
+    e.n_cand = sm.n_cand;
+    c->last = e;
+    if (sm.it < s.trace_cap) s.trace[sm.it] = e;
     c->remaining = sm.remaining;
     c->iter = sm.it + 1;
     c->n_valid = sm.n_cand + sm.newly;
-    c->evals += (unsigned long long)sm.n_cand * (unsigned long long)sm.n_known;
-    c->px = -1;
-    c->py = -1;
-    if (sm.remaining > 0) {
-      if (sm.next_key == 0ull) {
-        c->status = INPAINT_ERR_INTERNAL;  // Omega non-empty but no front
-      } else {
-        c->px = sm.next_idx % s.W;
-        c->py = sm.next_idx / s.W;
-        c->prio = __longlong_as_double((long long)(sm.next_key - 1ull));
-        c->conf = __ldcg(&s.pconf[sm.next_idx]);
-      }
+    atomicAdd(&c->evals, (unsigned long long)sm.n_cand * (unsigned long long)sm.n_known);
+    if (!next) {
+      c->px = -1;
+      c->py = -1;
+      if (sm.remaining > 0) c->status = INPAINT_ERR_INTERNAL;  // Omega non-empty but no front
     }
+  }
+  if (next && (int)threadIdx.x == (blockDim.x > 32 ? 32 : 0)) {
+    // the next target, from another warp (its confidence is a global read)
+    c->px = sm.next_idx % s.W;
+    c->py = sm.next_idx / s.W;
+    c->prio = __longlong_as_double((long long)(sm.next_key - 1ull));
+    c->conf = __ldcg(&s.pconf[sm.next_idx]);
   }
   __syncthreads();
 }
