@@ -403,9 +403,12 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       const int tx = px + tid % P - R, ty = py + tid / P - R;
       uint32_t w = 0;
       int known = 0;
-      if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H && __ldcg(&s.omega[(size_t)ty * s.W + tx]) == 0) {
-        w = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
-        known = 1;
+      if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H) {
+        // both reads in flight together; the pixel is kept only if known
+        const uint8_t o = __ldcg(&s.omega[(size_t)ty * s.W + tx]);
+        const uint32_t v = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
+        known = o == 0;
+        w = known ? v : 0u;
       }
       tgt[(tid / P) * G::TP + tid % P] = w;
       tl.known[tid] = (uint8_t)known;
@@ -501,6 +504,15 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   // publication of the next round, bookkeeping.  Whole block.
   auto lead_round = [&](int px, int py, bool searches) {
     const unsigned long long t_a = globaltimer();
+    // the stop decision's global inputs, read now so that their latency
+    // hides behind the phases (a stop seen here ends the loop one iteration
+    // later at most)
+    int lim = 0, status = 0, err = 0;
+    if (tid == 0) {
+      lim = __ldcg(&c->iter_limit);
+      status = __ldcg(&c->status);
+      err = __ldcg(ea.err);
+    }
     spec_phase<R>(s, usm, uca, staged);
     if (searches) {
       const unsigned long long best = search_round(px, py);
@@ -519,7 +531,6 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
         // Thread 0 decides (the inputs are global and may change under
         // other threads' feet) and the barrier below shares the decision.
         if (tid == 0) {
-          const int lim = __ldcg(&c->iter_limit), status = __ldcg(&c->status), err = __ldcg(ea.err);
           bool st = usm.remaining <= 0 || usm.next_key == 0ull || usm.it + 1 >= lim || status != 0 ||
                     err != 0;
           if (!st && ea.tick_ns && globaltimer() - x.t_start > ea.tick_ns) {
@@ -542,9 +553,9 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       tl.py = npy;
     }
     staged = ok && !stop;
-    if (staged) stage_nbhd<R, true, true>(s, npx, npy, usm);  // next speculative phase's input
+    if (staged) stage_next<R>(s, npx, npy, usm);  // next speculative phase's input
     if (ok) {
-      update_finish<R>(s, usm);
+      update_finish<R>(s, usm, staged);
       if (tid == 0) {
         atomicAdd(&c->t_search, t_b - t_a);
         atomicAdd(&c->t_update, globaltimer() - t_b);
@@ -619,7 +630,7 @@ __global__ void __launch_bounds__(kEngThreads) k_update_fast(ImgState s, cudaGra
   }
   spec_phase<R>(s, usm, uca, false);
   const bool ok = update_phase<R>(s, s.partial, s.n_partial, usm, uca);
-  if (ok) update_finish<R>(s, usm);
+  if (ok) update_finish<R>(s, usm, false);
   if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, ok && loop_active(s.ctrl) ? 1u : 0u);
 }
 

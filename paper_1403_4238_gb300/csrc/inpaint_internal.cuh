@@ -151,6 +151,13 @@ __device__ inline bool prio_better(unsigned long long ka, int ia, unsigned long 
   return ka > kb || (ka == kb && ia < ib);
 }
 
+// (k, i) = the better of (k, i) and (kk, ii), without a branch.
+__device__ __forceinline__ void prio_take(unsigned long long& k, int& i, unsigned long long kk, int ii) {
+  const bool b = prio_better(kk, ii, k, i);
+  k = b ? kk : k;
+  i = b ? ii : i;
+}
+
 __device__ inline unsigned long long warp_min_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -165,10 +172,7 @@ __device__ inline void warp_best_prio(unsigned long long& k, int& i) {
   for (int o = 16; o > 0; o >>= 1) {
     unsigned long long tk = __shfl_xor_sync(0xffffffffu, k, o);
     int ti = __shfl_xor_sync(0xffffffffu, i, o);
-    if (prio_better(tk, ti, k, i)) {
-      k = tk;
-      i = ti;
-    }
+    prio_take(k, i, tk, ti);
   }
 }
 
@@ -197,19 +201,16 @@ __device__ inline void block_best_prio(unsigned long long& k, int& i, PrioBest* 
   i = scratch[0].idx;
 }
 
+// Block reductions: one value per warp in scratch, then every warp reduces
+// those itself (no lone warp between two barriers).  The leading barrier
+// keeps the previous call's readers ahead of this call's writers.
 __device__ inline unsigned long long block_min_u64(unsigned long long v, unsigned long long* scratch) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_min_u64(v);
   __syncthreads();
   if (lane == 0) scratch[wid] = v;
   __syncthreads();
-  if (wid == 0) {
-    unsigned long long t = lane < nw ? scratch[lane] : ~0ull;
-    t = warp_min_u64(t);
-    if (lane == 0) scratch[0] = t;
-  }
-  __syncthreads();
-  return scratch[0];
+  return warp_min_u64(lane < nw ? scratch[lane] : ~0ull);
 }
 
 __device__ inline int block_sum_int(int v, int* scratch) {
@@ -219,14 +220,10 @@ __device__ inline int block_sum_int(int v, int* scratch) {
   __syncthreads();
   if (lane == 0) scratch[wid] = v;
   __syncthreads();
-  if (wid == 0) {
-    int t = lane < nw ? scratch[lane] : 0;
+  int t = lane < nw ? scratch[lane] : 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) scratch[0] = t;
-  }
-  __syncthreads();
-  return scratch[0];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
 }
 
 // ---- priority tiles: two-level argmax structure over the prio keys ----
@@ -248,11 +245,7 @@ __device__ inline void warp_rescan_t0(const ImgState& s, int tx, int ty) {
   unsigned long long k = 0ull;
   int idx = 0x7fffffff;
 #pragma unroll
-  for (int t = 0; t < N; ++t)
-    if (prio_better(kk[t], ii[t], k, idx)) {
-      k = kk[t];
-      idx = ii[t];
-    }
+  for (int t = 0; t < N; ++t) prio_take(k, idx, kk[t], ii[t]);
   warp_best_prio(k, idx);
   if (lane == 0) {
     s.tiles0[ty * s.t0x + tx].key = k;
@@ -280,11 +273,7 @@ __device__ inline void warp_rescan_t1(const ImgState& s, int ux, int uy) {
   unsigned long long k = 0ull;
   int idx = 0x7fffffff;
 #pragma unroll
-  for (int t = 0; t < N; ++t)
-    if (prio_better(kk[t], ii[t], k, idx)) {
-      k = kk[t];
-      idx = ii[t];
-    }
+  for (int t = 0; t < N; ++t) prio_take(k, idx, kk[t], ii[t]);
   warp_best_prio(k, idx);
   if (lane == 0) {
     s.tiles1[uy * s.t1x + ux].key = k;
@@ -302,10 +291,7 @@ __device__ inline void warp_global_best(const ImgState& s, unsigned long long& k
   for (int j = lane; j < n; j += 32) {
     const unsigned long long bk = __ldcg(&s.tiles1[j].key);
     const int bi = __ldcg(&s.tiles1[j].idx);
-    if (prio_better(bk, bi, k, idx)) {
-      k = bk;
-      idx = bi;
-    }
+    prio_take(k, idx, bk, bi);
   }
   warp_best_prio(k, idx);
 }

@@ -74,6 +74,9 @@ struct __align__(16) UpdSmem {
   unsigned long long red64[32];
   int red32[32];
   int spec_iter, spec_filled, nfront;  // speculative phase outcome
+  // the next target as staged by stage_next: centre, iteration, C(p^)
+  int nx_px, nx_py, nx_it;
+  double nx_cp;
   // outcome of update_phase, consumed by update_finish
   unsigned long long next_key;  // priority key of the next target (0: none)
   int next_idx;
@@ -173,19 +176,33 @@ template <int R, bool GRAY, bool CONF>
 __device__ inline void stage_nbhd(const ImgState& s, int cx, int cy, UpdSmem<R>& sm) {
   using G = UpdGeom<R>;
   constexpr int RB = G::RB, NS = G::NS;
-  for (int i = threadIdx.x; i < NS * NS; i += blockDim.x) {
-    const int x = cx - RB + i % NS, y = cy - RB + i / NS;
-    uint8_t o = 2, g = 0;
-    double cf = 0.0;
-    if (x >= 0 && x < s.W && y >= 0 && y < s.H) {
-      const size_t q = (size_t)y * s.W + x;
-      o = __ldcg(&s.omega[q]);
-      if (GRAY) g = __ldcg(&s.gray[q]);
-      if (CONF) cf = o ? 0.0 : __ldcg(&s.conf[q]);
+  constexpr int U = 4;  // entries per thread with their loads in flight together
+  const int step = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < NS * NS; i0 += U * step) {
+    uint8_t o[U], g[U];
+    double cf[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * step;
+      const int x = cx - RB + i % NS, y = cy - RB + i / NS;
+      o[u] = 2;
+      g[u] = 0;
+      cf[u] = 0.0;
+      if (i < NS * NS && x >= 0 && x < s.W && y >= 0 && y < s.H) {
+        const size_t q = (size_t)y * s.W + x;
+        o[u] = __ldcg(&s.omega[q]);
+        if (GRAY) g[u] = __ldcg(&s.gray[q]);
+        if (CONF) cf[u] = __ldcg(&s.conf[q]);  // read unconditionally, kept for known pixels
+      }
     }
-    sm.om[i] = o;
-    if (GRAY) sm.gr[i] = g;
-    if (CONF) sm.cf[i] = cf;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * step;
+      if (i >= NS * NS) break;
+      sm.om[i] = o[u];
+      if (GRAY) sm.gr[i] = g[u];
+      if (CONF) sm.cf[i] = o[u] ? 0.0 : cf[u];
+    }
   }
 }
 
@@ -250,11 +267,9 @@ __global__ void __launch_bounds__(256, 2) k_prio_init_fast(ImgState s) {
 // Loads what the update phase of target (px, py) reads but the search does
 // not change (see UpdCache), with threads [first, blockDim.x).  No barrier.
 template <int R>
-__device__ void update_prefetch(const ImgState& s, UpdCache<R>& ca, int first) {
+__device__ void update_prefetch(const ImgState& s, UpdCache<R>& ca, int first, int px, int py) {
   using G = UpdGeom<R>;
   constexpr int R2 = G::R2, NC = G::NC;
-  const Ctrl* c = s.ctrl;
-  const int px = __ldcg(&c->px), py = __ldcg(&c->py);
   const int W = s.W, H = s.H;
   const int tx0 = max(0, px - R2) / kT0, tx1 = min(W - 1, px + R2) / kT0;
   const int ty0 = max(0, py - R2) / kT0, ty1 = min(H - 1, py + R2) / kT0;
@@ -352,6 +367,27 @@ __device__ inline void warp_fsat(UpdSmem<R>& sm) {
     for (int v = 2; v <= P; ++v) sm.fsat[v * P1 + u] += sm.fsat[(v - 1) * P1 + u];
 }
 
+// The next iteration's input, once update_phase has selected the next
+// target (npx, npy): its neighbourhood, and in sm.nx_* its centre,
+// iteration number and confidence C(p^), so that spec_phase(staged = true)
+// reads no global control state.  The thread that reads C(p^) also installs
+// it in the control block.  Whole block; the caller's barrier makes it
+// visible.
+template <int R>
+__device__ void stage_next(const ImgState& s, int npx, int npy, UpdSmem<R>& sm) {
+  const int t_cp = (int)blockDim.x - 1;  // a thread with the fewest staging entries
+  double ncp = 0.0;
+  if ((int)threadIdx.x == t_cp) ncp = __ldcg(&s.pconf[sm.next_idx]);
+  stage_nbhd<R, true, true>(s, npx, npy, sm);
+  if ((int)threadIdx.x == t_cp) {
+    sm.nx_px = npx;
+    sm.nx_py = npy;
+    sm.nx_it = sm.it + 1;
+    sm.nx_cp = ncp;
+    s.ctrl->conf = ncp;
+  }
+}
+
 // Speculative phase: post-fill mask, grey levels and confidences of the
 // neighbourhood of p^, the filled set and its integral image, the post-fill
 // front of the window with its normals and confidence terms.  Everything
@@ -363,9 +399,18 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW;
   const Ctrl* c = s.ctrl;
-  const int px = __ldcg(&c->px), py = __ldcg(&c->py), it = __ldcg(&c->iter);
-  const double cp = __ldcg(&c->conf);
-  if (!staged) {
+  int px, py, it;
+  double cp;
+  if (staged) {
+    px = sm.nx_px;
+    py = sm.nx_py;
+    it = sm.nx_it;
+    cp = sm.nx_cp;
+  } else {
+    px = __ldcg(&c->px);
+    py = __ldcg(&c->py);
+    it = __ldcg(&c->iter);
+    cp = __ldcg(&c->conf);
     stage_nbhd<R, true, true>(s, px, py, sm);
     __syncthreads();
   }
@@ -412,7 +457,7 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
   const bool spare = nchain + 64 <= nt;  // at least two warps without chains
   const int fsat_warp = spare ? nchain / 32 : 0;
   if ((int)(threadIdx.x >> 5) == fsat_warp) warp_fsat<R>(sm);
-  update_prefetch<R>(s, ca, spare ? nchain + 32 : 0);
+  update_prefetch<R>(s, ca, spare ? nchain + 32 : 0, px, py);
   if (threadIdx.x == 0) {
     sm.nfront = nfront;
     sm.spec_iter = it;
@@ -589,10 +634,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       const int x = tx * kT0 + (j & (kT0 - 1)), y = ty * kT0 + j / kT0;
       const unsigned long long kk = ca.tp[t * (kT0 * kT0) + j];
       const int ii = y * W + x;
-      if (prio_better(kk, ii, k, idx)) {
-        k = kk;
-        idx = ii;
-      }
+      prio_take(k, idx, kk, ii);
     }
     warp_best_prio(k, idx);
     if (lane == 0) {
@@ -612,10 +654,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
 #pragma unroll
     for (int r8 = 0; r8 < kT1 * kT1 / 32; ++r8) {
       const PrioBest& e = ca.t0c[u * (kT1 * kT1) + lane + 32 * r8];
-      if (prio_better(e.key, e.idx, k, idx)) {
-        k = e.key;
-        idx = e.idx;
-      }
+      prio_take(k, idx, e.key, e.idx);
     }
     warp_best_prio(k, idx);
     if (lane == 0) {
@@ -629,16 +668,14 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   }
   __syncthreads();
   remaining -= filled;
-  if (tid < 32) {
+  {
+    // every warp takes the same decision: a lone warp running while the
+    // others wait at the barrier was several times slower here
     unsigned long long k = 0ull;
     int idx = 0x7fffffff;
     if (remaining > 0) {
       if (ca.t1n) {
-        for (int j = lane; j < ca.t1n; j += 32)
-          if (prio_better(ca.t1c[j].key, ca.t1c[j].idx, k, idx)) {
-            k = ca.t1c[j].key;
-            idx = ca.t1c[j].idx;
-          }
+        for (int j = lane; j < ca.t1n; j += 32) prio_take(k, idx, ca.t1c[j].key, ca.t1c[j].idx);
         warp_best_prio(k, idx);
       } else {
         warp_global_best(s, k, idx);
@@ -668,11 +705,12 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
 
 // Records the iteration applied by update_phase (trace, counters) and
 // installs the next target p^ with its priority and confidence in the
-// control block.  Neither the image state nor the tiles change here, so the
+// control block (stage_next has installed the confidence when
+// `cp_staged`).  Neither the image state nor the tiles change here, so the
 // persistent engine publishes the next target to its searchers first.
 // Whole block; ends with a __syncthreads.
 template <int R>
-__device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm) {
+__device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm, bool cp_staged) {
   Ctrl* c = s.ctrl;
   const bool next = sm.remaining > 0 && sm.next_key != 0ull;
   if (threadIdx.x == 0) {
@@ -708,7 +746,7 @@ __device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm) {
     c->px = sm.next_idx % s.W;
     c->py = sm.next_idx / s.W;
     c->prio = __longlong_as_double((long long)(sm.next_key - 1ull));
-    c->conf = __ldcg(&s.pconf[sm.next_idx]);
+    if (!cp_staged) c->conf = __ldcg(&s.pconf[sm.next_idx]);
   }
   __syncthreads();
 }
