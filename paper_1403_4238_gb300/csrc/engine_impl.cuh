@@ -256,6 +256,14 @@ __device__ inline void st_release64(unsigned long long* p, unsigned long long v)
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+__device__ inline void st_relaxed64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// The leader's publishing thread: the last one, in a warp with no level-0
+// tile to scan in most iterations, so that its fence waits off the path.
+constexpr int kPubThread = kEngThreads - 1;
+
 __device__ inline void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -518,14 +526,17 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       const unsigned long long best = search_round(px, py);
       if (tid == 0) tpart[rank] = best;
     }
-    if (tid == 0) tl.flag = wait_arrivals(tc, n_wait, ea.err, limit);
+    if (tid == 0) {
+      tl.flag = wait_arrivals(tc, n_wait, ea.err, limit);
+      tc->arrive = 0u;  // all keys are in; ordered before the next publication by its fence
+    }
     __syncthreads();
     bool stop = true, ok = false;
     int npx = 0, npy = 0;
     unsigned long long t_b = 0ull;
     if (tl.flag) {
       t_b = globaltimer();
-      ok = update_phase<R>(s, tpart, ns, usm, uca);  // ends with a __syncthreads
+      ok = update_phase<R>(s, tpart, ns, usm, uca, kPubThread);  // ends with a __syncthreads
       if (ok) {
         // the next target is known: publish it before the bookkeeping.
         // Thread 0 decides (the inputs are global and may change under
@@ -545,9 +556,16 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     }
     __syncthreads();
     stop = ok ? tl.stop != 0 : true;
+    // publication: the update phase's fence (same thread) already ordered
+    // every write the searchers read before this store; without an update
+    // (timeout or error) the store carries its own release
+    if (tid == kPubThread) {
+      if (ok)
+        st_relaxed64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
+      else
+        st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
+    }
     if (tid == 0) {
-      tc->arrive = 0u;
-      st_release64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
       tl.stop = stop;
       tl.px = npx;
       tl.py = npy;

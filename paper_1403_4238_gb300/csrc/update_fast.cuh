@@ -470,9 +470,12 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
 // of partial[0..n_partial), on the state prepared by spec_phase and
 // update_prefetch.  Returns false (status written) when there is no source
 // patch or the state is inconsistent.  Whole block; ends with a __syncthreads.
+// Thread `fence_thread` (if any) issues a gpu-scope fence once the pixel,
+// mask and count writes of the iteration are issued (see the engine's
+// publication).
 template <int R>
 __device__ bool update_phase(const ImgState& s, const unsigned long long* partial, int n_partial,
-                             UpdSmem<R>& sm, UpdCache<R>& ca) {
+                             UpdSmem<R>& sm, UpdCache<R>& ca, int fence_thread = -1) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW, NC = G::NC;
   Ctrl* c = s.ctrl;
@@ -621,6 +624,10 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     }
   }
   newly = block_sum_int(newly, sm.red32);  // includes __syncthreads
+  // every write the next search reads (pixels, mask, validity counts) is
+  // issued: the publishing thread fences them now, while the tiles are
+  // computed, so that its publication later needs no wait of its own
+  if ((int)threadIdx.x == fence_thread) asm volatile("fence.acq_rel.gpu;" ::: "memory");
 
   // level-0 tiles from the cached keys, then level-1, then the best
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
