@@ -177,8 +177,8 @@ EVALS_PER_CLK_SM = 64
 
 # DRAM bytes (read + write) of one k_engine launch on the headline workload,
 # from an ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum: 2.318 MB + 2.032 MB); None once the kernel changes.
-ENGINE_TRAFFIC_BYTES = 4349696
+# dram__bytes_write.sum: 2.359 MB + 1.737 MB); None once the kernel changes.
+ENGINE_TRAFFIC_BYTES = 4095488
 
 
 def measured_peaks():
