@@ -200,6 +200,59 @@ def serving_case(W, H, r, lo, s) -> Case:
     return Case(f"req_{W}x{H}_r{r}", image(W, H, 12, 30.0, s), ellipse_mask(W, H, 3, lo, lo + 0.005, s + 1), r)
 
 
+def box_shape_mask(W: int, H: int, w: int, h: int, kind: str, seed: int) -> np.ndarray:
+    """A w x h object at a seeded position inside the image, with bounding box
+    exactly w x h: "blob" = the inscribed ellipse, "random" = a seeded union
+    of discs inside the box (four of them centred on its edge midpoints, so
+    that the shape spans the box), "strip" = the full box."""
+    g = _rng(seed)
+    x0 = int(g.integers(0, W - w + 1))
+    y0 = int(g.integers(0, H - h + 1))
+    m = np.zeros((H, W), bool)
+    ys, xs = np.mgrid[0:h, 0:w].astype(np.float64)
+    if kind == "strip":
+        box = np.ones((h, w), bool)
+    elif kind == "blob":
+        cx, cy = (w - 1) / 2.0, (h - 1) / 2.0
+        box = ((xs - cx) / (w / 2.0)) ** 2 + ((ys - cy) / (h / 2.0)) ** 2 <= 1.0
+    elif kind == "random":
+        rad0 = 0.12 * min(w, h)
+        centres = [((w - 1) / 2.0, 0.0), ((w - 1) / 2.0, h - 1.0), (0.0, (h - 1) / 2.0), (w - 1.0, (h - 1) / 2.0)]
+        radii = [rad0] * 4
+        for _ in range(24):
+            centres.append((g.uniform(0, w - 1), g.uniform(0, h - 1)))
+            radii.append(g.uniform(0.5, 1.5) * 2.0 * rad0)
+        box = np.zeros((h, w), bool)
+        for (cx, cy), rad in zip(centres, radii):
+            box |= (xs - cx) ** 2 + (ys - cy) ** 2 <= rad * rad
+    else:
+        raise ValueError(kind)
+    m[y0:y0 + h, x0:x0 + w] = box
+    return m.astype(np.uint8)
+
+
+# Test images of Table 3: (name, W, H, object kind, object w, object h,
+# image regions, grating amplitude).  Object kinds: blob, small blob, big /
+# random shape, long strip.
+TABLE3 = (
+    ("walkingman", 512, 384, "blob", 78, 126, 12, 30.0),
+    ("river", 480, 639, "blob", 59, 93, 16, 40.0),
+    ("divingman", 576, 384, "random", 155, 186, 8, 40.0),
+    ("hill", 1024, 550, "strip", 1024, 10, 12, 30.0),
+)
+
+
+def table3_case(name: str, r: int = 4, seed: int = 7) -> Case:
+    """Synthetic stand-in for one test image of Table 3 (its size, object
+    type and object size), with patch radius r."""
+    for k, (nm, W, H, kind, w, h, regions, amp) in enumerate(TABLE3):
+        if nm == name:
+            s = seed + 100 * k
+            return Case(f"{nm}{W}x{H}_r{r}", image(W, H, regions, amp, s),
+                        box_shape_mask(W, H, w, h, kind, s + 1), r)
+    raise KeyError(name)
+
+
 def tiny(W: int, H: int, seed: int, hole: tuple | None = None, r: int = 1) -> Case:
     """Small random case for brute-force checks: noise image plus a hole."""
     g = _rng(seed)
