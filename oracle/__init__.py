@@ -116,6 +116,14 @@ def _load():
         lib.oracle_run_from_state.argtypes = [u8p, u8p, f64p, c_int, c_int, c_int, c_int, c_int,
                                               c_int, c_int, c_int, ctypes.POINTER(Trace), c_int,
                                               i32p, u64p]
+        lib.oracle_ssd_map_overlap.restype = c_int
+        lib.oracle_ssd_map_overlap.argtypes = lib.oracle_ssd_map.argtypes
+        lib.oracle_search_rect2.restype = None
+        lib.oracle_search_rect2.argtypes = [u8p, c_int, c_int, c_int, c_double, c_int, i32p, i32p, i32p,
+                                            i32p]
+        lib.oracle_run2.restype = c_int
+        lib.oracle_run2.argtypes = [u8p, u8p, c_int, c_int, c_int, c_double, c_int, c_int, u8p, u8p,
+                                    f64p, ctypes.POINTER(Trace), c_int, i32p, u64p]
         _lib = lib
         return lib
 
@@ -150,26 +158,28 @@ def priority(gray_img, conf, omega, r, x, y):
     return p, co.value, do.value
 
 
-def search_rect(mask, r, alpha=-1.0):
+def search_rect(mask, r, alpha=-1.0, overlap=False):
     H, W = mask.shape
     m = np.ascontiguousarray(mask, dtype=np.uint8)
     v = [ctypes.c_int32() for _ in range(4)]
-    _load().oracle_search_rect(_ptr(m, ctypes.c_uint8), W, H, r, float(alpha),
-                               *[ctypes.byref(x) for x in v])
+    _load().oracle_search_rect2(_ptr(m, ctypes.c_uint8), W, H, r, float(alpha), int(bool(overlap)),
+                                *[ctypes.byref(x) for x in v])
     return tuple(x.value for x in v)
 
 
-def ssd_map(rgb, omega, r, px, py, rect=None):
-    """SSD of every candidate centre (UINT32_MAX where invalid), n_cand, |K|."""
+def ssd_map(rgb, omega, r, px, py, rect=None, overlap=False):
+    """SSD of every candidate centre (UINT32_MAX where invalid), n_cand, |K|
+    (overlap: the partial-overlap variant)."""
     H, W = omega.shape
     img = np.ascontiguousarray(rgb, dtype=np.uint8)
     om = np.ascontiguousarray(omega, dtype=np.uint8)
     if rect is None:
-        rect = (r, W - 1 - r, r, H - 1 - r)
+        rect = (0, W - 1, 0, H - 1) if overlap else (r, W - 1 - r, r, H - 1 - r)
     out = np.zeros((H, W), np.uint32)
     nk = ctypes.c_int32()
-    nc = _load().oracle_ssd_map(_ptr(img, ctypes.c_uint8), _ptr(om, ctypes.c_uint8), W, H, r,
-                                px, py, *rect, _ptr(out, ctypes.c_uint32), ctypes.byref(nk))
+    fn = _load().oracle_ssd_map_overlap if overlap else _load().oracle_ssd_map
+    nc = fn(_ptr(img, ctypes.c_uint8), _ptr(om, ctypes.c_uint8), W, H, r,
+            px, py, *rect, _ptr(out, ctypes.c_uint32), ctypes.byref(nk))
     return out, int(nc), int(nk.value)
 
 
@@ -184,8 +194,9 @@ class Result:
         self.evals = evals
 
 
-def run(rgb, mask, r, alpha=-1.0, max_iters=0, trace_cap=None) -> Result:
-    """The whole removal loop.  rgb: (H, W, 3) uint8, mask: (H, W) nonzero = remove."""
+def run(rgb, mask, r, alpha=-1.0, max_iters=0, trace_cap=None, overlap=False) -> Result:
+    """The whole removal loop.  rgb: (H, W, 3) uint8, mask: (H, W) nonzero = remove;
+    overlap: the partial-overlap search variant (Alg. 1, Sec. 5.4)."""
     H, W = mask.shape
     img = np.ascontiguousarray(rgb, dtype=np.uint8)
     m = np.ascontiguousarray(mask, dtype=np.uint8)
@@ -197,11 +208,11 @@ def run(rgb, mask, r, alpha=-1.0, max_iters=0, trace_cap=None) -> Result:
     tr = np.zeros(max(trace_cap, 1), TRACE_DTYPE)
     iters = ctypes.c_int32()
     evals = ctypes.c_uint64()
-    st = _load().oracle_run(_ptr(img, ctypes.c_uint8), _ptr(m, ctypes.c_uint8), W, H, r,
-                            float(alpha), int(max_iters), _ptr(rgb_out, ctypes.c_uint8),
-                            _ptr(mask_out, ctypes.c_uint8), _ptr(conf_out, ctypes.c_double),
-                            tr.ctypes.data_as(ctypes.POINTER(Trace)), trace_cap,
-                            ctypes.byref(iters), ctypes.byref(evals))
+    st = _load().oracle_run2(_ptr(img, ctypes.c_uint8), _ptr(m, ctypes.c_uint8), W, H, r,
+                             float(alpha), int(bool(overlap)), int(max_iters),
+                             _ptr(rgb_out, ctypes.c_uint8), _ptr(mask_out, ctypes.c_uint8),
+                             _ptr(conf_out, ctypes.c_double), tr.ctypes.data_as(ctypes.POINTER(Trace)),
+                             trace_cap, ctypes.byref(iters), ctypes.byref(evals))
     n = iters.value
     return Result(st, rgb_out, mask_out, conf_out, tr[: min(n, trace_cap)].copy(), n,
                   int(evals.value))

@@ -130,7 +130,20 @@ double oracle_priority(const uint8_t* gray, const double* conf,
 
 void oracle_search_rect(const uint8_t* mask, int W, int H, int r, double alpha,
                         int* cx0, int* cx1, int* cy0, int* cy1) {
+  oracle_search_rect2(mask, W, H, r, alpha, 0, cx0, cx1, cy0, cy1);
+}
+
+void oracle_search_rect2(const uint8_t* mask, int W, int H, int r, double alpha,
+                         int overlap, int* cx0, int* cx1, int* cy0, int* cy1) {
+  /* Candidates whose patch crosses the image border exist only in the
+   * partial-overlap variant: there the rectangle is clamped to the image. */
   int lo_x = r, hi_x = W - 1 - r, lo_y = r, hi_y = H - 1 - r;
+  if (overlap) {
+    lo_x = 0;
+    hi_x = W - 1;
+    lo_y = 0;
+    hi_y = H - 1;
+  }
   if (alpha >= 0.0) {
     /* Bounding box of the object (Sec. 5.3): w x h. */
     int x0 = W, x1 = -1, y0 = H, y1 = -1;
@@ -203,10 +216,68 @@ int oracle_ssd_map(const uint8_t* rgb, const uint8_t* omega, int W, int H,
   return n_cand;
 }
 
+int oracle_ssd_map_overlap(const uint8_t* rgb, const uint8_t* omega, int W,
+                           int H, int r, int px, int py, int cx0, int cx1,
+                           int cy0, int cy1, uint32_t* ssd_out, int* n_known) {
+  int nk = 0;
+  for (int dy = -r; dy <= r; ++dy)
+    for (int dx = -r; dx <= r; ++dx)
+      if (known(omega, px + dx, py + dy, W, H)) ++nk;
+  if (n_known) *n_known = nk;
+
+  int n_cand = 0;
+  for (int qy = 0; qy < H; ++qy)
+    for (int qx = 0; qx < W; ++qx) {
+      size_t qi = (size_t)qy * W + qx;
+      ssd_out[qi] = UINT32_MAX;
+      if (qx < cx0 || qx > cx1 || qy < cy0 || qy > cy1) continue;
+      /* The copy needs a known source pixel under every unknown in-image
+       * pixel of the target patch. */
+      int ok = 1;
+      for (int dy = -r; dy <= r && ok; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+          int tx = px + dx, ty = py + dy;
+          if (!in_image(tx, ty, W, H) || !omega[(size_t)ty * W + tx]) continue;
+          if (!known(omega, qx + dx, qy + dy, W, H)) {
+            ok = 0;
+            break;
+          }
+        }
+      if (!ok) continue;
+      ++n_cand;
+      /* Alg. 1 / Sec. 5.4: squared RGB differences over the pixel pairs
+       * with both the target pixel and the source pixel known and in the
+       * image (an empty sum is 0). */
+      uint64_t s = 0;
+      for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+          if (!known(omega, px + dx, py + dy, W, H)) continue;
+          if (!known(omega, qx + dx, qy + dy, W, H)) continue;
+          const uint8_t* a = rgb + 3 * ((size_t)(py + dy) * W + px + dx);
+          const uint8_t* b = rgb + 3 * ((size_t)(qy + dy) * W + qx + dx);
+          for (int c = 0; c < 3; ++c) {
+            int64_t e = (int64_t)a[c] - (int64_t)b[c];
+            s += (uint64_t)(e * e);
+          }
+        }
+      ssd_out[qi] = (uint32_t)s;
+    }
+  return n_cand;
+}
+
 int oracle_run_from_state(uint8_t* rgb, uint8_t* omega, double* conf, int W,
                           int H, int r, int cx0, int cx1, int cy0, int cy1,
                           int max_iters, oracle_trace* trace, int trace_cap,
                           int* iters_done, uint64_t* evals) {
+  return oracle_run_from_state2(rgb, omega, conf, W, H, r, cx0, cx1, cy0, cy1,
+                                0, max_iters, trace, trace_cap, iters_done,
+                                evals);
+}
+
+int oracle_run_from_state2(uint8_t* rgb, uint8_t* omega, double* conf, int W,
+                           int H, int r, int cx0, int cx1, int cy0, int cy1,
+                           int overlap, int max_iters, oracle_trace* trace,
+                           int trace_cap, int* iters_done, uint64_t* evals) {
   size_t n = (size_t)W * H;
   int it = 0;
   uint64_t ev = 0;
@@ -254,8 +325,10 @@ int oracle_run_from_state(uint8_t* rgb, uint8_t* omega, double* conf, int W,
 
     /* 3. findBestPatch: q~ = argmin SSD, ties to the lowest index (Eq. 3). */
     int nk = 0;
-    int n_cand = oracle_ssd_map(rgb, omega, W, H, r, px, py, cx0, cx1, cy0,
-                                cy1, ssd, &nk);
+    int n_cand = overlap ? oracle_ssd_map_overlap(rgb, omega, W, H, r, px, py,
+                                                  cx0, cx1, cy0, cy1, ssd, &nk)
+                         : oracle_ssd_map(rgb, omega, W, H, r, px, py, cx0,
+                                          cx1, cy0, cy1, ssd, &nk);
     long bq = -1;
     for (size_t i = 0; i < n; ++i)
       if (ssd[i] != UINT32_MAX && (bq < 0 || ssd[i] < ssd[bq])) bq = (long)i;
@@ -314,6 +387,14 @@ int oracle_run(const uint8_t* rgb, const uint8_t* mask, int W, int H, int r,
                double alpha, int max_iters, uint8_t* rgb_out,
                uint8_t* mask_out, double* conf_out, oracle_trace* trace,
                int trace_cap, int* iters_done, uint64_t* evals) {
+  return oracle_run2(rgb, mask, W, H, r, alpha, 0, max_iters, rgb_out,
+                     mask_out, conf_out, trace, trace_cap, iters_done, evals);
+}
+
+int oracle_run2(const uint8_t* rgb, const uint8_t* mask, int W, int H, int r,
+                double alpha, int overlap, int max_iters, uint8_t* rgb_out,
+                uint8_t* mask_out, double* conf_out, oracle_trace* trace,
+                int trace_cap, int* iters_done, uint64_t* evals) {
   if (iters_done) *iters_done = 0;
   if (evals) *evals = 0;
   if (!rgb || !mask || r < 1 || r > 32 || W < 2 * r + 1 || H < 2 * r + 1)
@@ -339,13 +420,13 @@ int oracle_run(const uint8_t* rgb, const uint8_t* mask, int W, int H, int r,
     conf[i] = mask[i] ? 0.0 : 1.0;
   }
   int cx0, cx1, cy0, cy1;
-  oracle_search_rect(mask, W, H, r, alpha, &cx0, &cx1, &cy0, &cy1);
+  oracle_search_rect2(mask, W, H, r, alpha, overlap, &cx0, &cx1, &cy0, &cy1);
 
   int status = ORACLE_DONE;
   if (n_omega > 0)
-    status = oracle_run_from_state(img, omega, conf, W, H, r, cx0, cx1, cy0,
-                                   cy1, max_iters, trace, trace_cap,
-                                   iters_done, evals);
+    status = oracle_run_from_state2(img, omega, conf, W, H, r, cx0, cx1, cy0,
+                                    cy1, overlap, max_iters, trace, trace_cap,
+                                    iters_done, evals);
   if (rgb_out) memcpy(rgb_out, img, 3 * n);
   if (mask_out) memcpy(mask_out, omega, n);
   if (conf_out) memcpy(conf_out, conf, n * sizeof(double));

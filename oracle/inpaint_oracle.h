@@ -75,6 +75,22 @@ int oracle_ssd_map(const uint8_t* rgb, const uint8_t* omega, int W, int H,
 void oracle_search_rect(const uint8_t* mask, int W, int H, int r, double alpha,
                         int* cx0, int* cx1, int* cy0, int* cy1);
 
+/* Partial-overlap variant of the search (Alg. 1 and Sec. 5.4): every centre
+ * of the rectangle is a candidate, also when its patch overlaps Omega or
+ * crosses the image border, provided a known in-image source pixel lies
+ * under every unknown in-image pixel of the target patch (so that the copy
+ * is defined).  SSD(q) sums the squared RGB differences over the offsets
+ * whose target pixel and source pixel are both known and in the image (0
+ * when there is none).  Same outputs as oracle_ssd_map. */
+int oracle_ssd_map_overlap(const uint8_t* rgb, const uint8_t* omega, int W,
+                           int H, int r, int px, int py, int cx0, int cx1,
+                           int cy0, int cy1, uint32_t* ssd_out, int* n_known);
+
+/* oracle_search_rect; with overlap != 0 the rectangle is clamped to the
+ * image instead of the interior centres (the partial-overlap variant). */
+void oracle_search_rect2(const uint8_t* mask, int W, int H, int r, double alpha,
+                         int overlap, int* cx0, int* cx1, int* cy0, int* cy1);
+
 /* The whole removal loop.  rgb_out (3*W*H), mask_out (W*H) and conf_out
  * (W*H) receive the final state when non-NULL; trace receives up to
  * trace_cap entries; *iters_done and *evals (sum over iterations of
@@ -93,6 +109,19 @@ int oracle_run_from_state(uint8_t* rgb, uint8_t* omega, double* conf, int W,
                           int H, int r, int cx0, int cx1, int cy0, int cy1,
                           int max_iters, oracle_trace* trace, int trace_cap,
                           int* iters_done, uint64_t* evals);
+
+/* oracle_run / oracle_run_from_state with the search variant chosen by
+ * `overlap` (0: candidates fully known and inside the image; 1: the
+ * partial-overlap variant of oracle_ssd_map_overlap).  The work count adds
+ * n_cand * n_known per iteration in both. */
+int oracle_run2(const uint8_t* rgb, const uint8_t* mask, int W, int H, int r,
+                double alpha, int overlap, int max_iters, uint8_t* rgb_out,
+                uint8_t* mask_out, double* conf_out, oracle_trace* trace,
+                int trace_cap, int* iters_done, uint64_t* evals);
+int oracle_run_from_state2(uint8_t* rgb, uint8_t* omega, double* conf, int W,
+                           int H, int r, int cx0, int cx1, int cy0, int cy1,
+                           int overlap, int max_iters, oracle_trace* trace,
+                           int trace_cap, int* iters_done, uint64_t* evals);
 
 #ifdef __cplusplus
 }

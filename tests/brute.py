@@ -97,6 +97,41 @@ def ssd_map(rgb, omega, r, px, py, rect=None):
     return out.astype(np.uint32), int(valid.sum()), nk
 
 
+def ssd_map_overlap(rgb, omega, r, px, py, rect=None):
+    """Partial-overlap variant (Alg. 1, Sec. 5.4) by whole-array shifts of a
+    padded frame: every centre of the image is a candidate if every unknown
+    in-image target pixel has a known in-image source pixel under it; the SSD
+    runs over the target/source pairs that are both known and in the image."""
+    H, W = omega.shape
+    P = 2 * r + 1
+    if rect is None:
+        rect = (0, W - 1, 0, H - 1)
+    # padded copies: outside the image = not known
+    kn = np.zeros((H + 2 * r, W + 2 * r), bool)
+    kn[r:r + H, r:r + W] = ~omega.astype(bool)
+    img = np.zeros((H + 2 * r, W + 2 * r, 3), np.int64)
+    img[r:r + H, r:r + W] = rgb
+    ssd = np.zeros((H, W), np.int64)
+    ok = np.ones((H, W), bool)
+    nk = 0
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            tx, ty = px + dx, py + dy
+            if not (0 <= tx < W and 0 <= ty < H):
+                continue
+            src_known = kn[r + dy:r + dy + H, r + dx:r + dx + W]  # known(q + d) for every centre q
+            if omega[ty, tx]:
+                ok &= src_known
+                continue
+            nk += 1
+            src = img[r + dy:r + dy + H, r + dx:r + dx + W, :]
+            ssd += np.where(src_known, ((src - rgb[ty, tx, :].astype(np.int64)) ** 2).sum(axis=-1), 0)
+    ys, xs = np.mgrid[0:H, 0:W]
+    ok &= (xs >= rect[0]) & (xs <= rect[1]) & (ys >= rect[2]) & (ys <= rect[3])
+    out = np.where(ok, ssd, 2**32 - 1)
+    return out.astype(np.uint32), int(ok.sum()), nk
+
+
 def argmin_lowest(a):
     """Index of the smallest entry; the lowest flat index among equals."""
     flat = a.reshape(-1)

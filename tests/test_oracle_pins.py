@@ -98,6 +98,74 @@ def test_ssd_map_matches_bruteforce(seed, r, W, H):
         assert (nc_a, nk_a) == (nc_b, nk_b)
 
 
+@pytest.mark.parametrize("seed,r,W,H", [(10, 1, 8, 8), (11, 2, 16, 12), (12, 1, 24, 16), (13, 2, 19, 23),
+                                         (14, 3, 20, 18), (15, 1, 9, 30)])
+def test_ssd_map_overlap_matches_bruteforce(seed, r, W, H):
+    # partial-overlap variant (Alg. 1, Sec. 5.4): candidates may overlap Omega
+    # and cross the image border
+    c = synth.tiny(W, H, seed, r=r)
+    om = c.mask
+    ys, xs = np.nonzero(brute.front(om))
+    for k in range(0, len(xs), max(1, len(xs) // 5)):
+        px, py = int(xs[k]), int(ys[k])
+        for rect in (None, (2, W - 3, 1, H - 2)):
+            a, nc_a, nk_a = oracle.ssd_map(c.rgb, om, r, px, py, rect=rect, overlap=True)
+            b, nc_b, nk_b = brute.ssd_map_overlap(c.rgb, om, r, px, py, rect=rect)
+            assert np.array_equal(a, b)
+            assert (nc_a, nk_a) == (nc_b, nk_b)
+
+
+def test_overlap_variant_admits_exactly_the_covering_candidates():
+    # 12 x 10 image, r = 1, one unknown pixel at (5, 5); target p^ = (5, 5)
+    rng = np.random.default_rng(3)
+    rgb = rng.integers(0, 256, (10, 12, 3)).astype(np.uint8)
+    om = np.zeros((10, 12), np.uint8)
+    om[5, 5] = 1
+    out, nc, nk = oracle.ssd_map(rgb, om, 1, 5, 5, overlap=True)
+    assert nk == 8
+    # every centre but the unknown pixel itself covers it with a known pixel
+    assert nc == 12 * 10 - 1 and out[5, 5] == 2**32 - 1
+    # a candidate next to the hole compares 7 pairs (its own (5, 5) pixel is unknown)
+    qx, qy = 6, 5
+    want = 0
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if (dx, dy) == (0, 0) or (qx + dx, qy + dy) == (5, 5):
+                continue
+            d = rgb[5 + dy, 5 + dx].astype(np.int64) - rgb[qy + dy, qx + dx].astype(np.int64)
+            want += int((d * d).sum())
+    assert out[qy, qx] == want
+    # a corner centre compares only the in-image pairs
+    d = rgb[5:7, 5:7].astype(np.int64) - rgb[0:2, 0:2].astype(np.int64)
+    d[0, 0] = 0  # target (5, 5) is unknown
+    assert out[0, 0] == int((d * d).sum())
+    # the default variant keeps only interior, fully known candidates
+    out0, nc0, _ = oracle.ssd_map(rgb, om, 1, 5, 5)
+    assert nc0 == 10 * 8 - 9 and out0[0, 0] == 2**32 - 1
+
+
+def test_overlap_variant_loop_invariants():
+    c = synth.small_rect(seed=5)
+    res = oracle.run(c.rgb, c.mask, c.r, overlap=True)
+    assert res.status == 0 and res.mask.sum() == 0
+    assert np.array_equal(res.rgb[c.mask == 0], c.rgb[c.mask == 0])  # known pixels never change
+    # each fill copies pixels that were known at that time: replaying the trace
+    # on the input reproduces the result
+    img = c.rgb.copy()
+    om = c.mask.astype(bool).copy()
+    r = c.r
+    for t in res.trace:
+        px, py, qx, qy = int(t["px"]), int(t["py"]), int(t["qx"]), int(t["qy"])
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                tx, ty = px + dx, py + dy
+                if 0 <= tx < c.W and 0 <= ty < c.H and om[ty, tx]:
+                    assert not om[qy + dy, qx + dx]
+                    img[ty, tx] = img[qy + dy, qx + dx]
+                    om[ty, tx] = False
+    assert np.array_equal(img, res.rgb)
+
+
 def test_planted_copy_found_exactly():
     rng = np.random.default_rng(7)
     W, H, r = 40, 30, 2
