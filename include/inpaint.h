@@ -91,7 +91,20 @@ typedef struct {
                             line with the image's radius and max_pixels >= the image's
                             pixels per CTA of its team (W*H / CTAs working on it)
                             gives rows_per_warp when tile_rows is 0 */
+  int search_variant;    /* INPAINT_SEARCH_FULL (default): candidate patches lie inside
+                            the image and inside the known region (Eq. 3-4);
+                            INPAINT_SEARCH_OVERLAP: the partial-overlap variant of
+                            Algorithm 1 / Sec. 5.4: every centre of the search rectangle
+                            (clamped to the image, not to the interior) is a candidate,
+                            its SSD runs over the offsets whose target and source pixels
+                            are both known and in the image, and it is admissible when a
+                            known in-image source pixel lies under every unknown in-image
+                            target pixel.  Plain form, patch_radius <= 8, graph loop
+                            (INPAINT_LOOP_AUTO picks it); not in batches or the server. */
 } inpaint_options;
+
+#define INPAINT_SEARCH_FULL 0
+#define INPAINT_SEARCH_OVERLAP 1
 
 #define INPAINT_LOOP_AUTO 0
 #define INPAINT_LOOP_ENGINE 1

@@ -127,7 +127,7 @@ class Options(ctypes.Structure):
         ("form", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("debug_checks", ctypes.c_int),
         ("search_alpha", ctypes.c_double), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p), ("loop_mode", ctypes.c_int), ("tile_rows", ctypes.c_int),
-        ("tuning_file", ctypes.c_char_p),
+        ("tuning_file", ctypes.c_char_p), ("search_variant", ctypes.c_int),
     ]
 
 

@@ -64,13 +64,16 @@ class Inpainter:
     of Eq. 6 (negative = exhaustive).  loop: "auto", "engine" (persistent
     kernel) or "graph" (conditional CUDA graph).  tile_rows: engine search
     unit height (0 = library choice); tuning_file: autotuner table
-    (paper_1403_4238_gb300.autotune) consulted when tile_rows is 0.  Inputs may be numpy arrays (host) or
-    CUDA torch tensors (device, uint8, contiguous).
+    (paper_1403_4238_gb300.autotune) consulted when tile_rows is 0.  overlap:
+    the partial-overlap search variant of Algorithm 1 / Sec. 5.4 (graph loop,
+    r <= 8).  Inputs may be numpy arrays (host) or CUDA torch tensors (device,
+    uint8, contiguous).
     """
 
     def __init__(self, rgb, mask, r: int, *, form: str = "plain", alpha: float = -1.0,
                  debug: bool = False, stream=None, torch_memory: bool = True,
-                 loop: str = "auto", tile_rows: int = 0, tuning_file: str | None = None):
+                 loop: str = "auto", tile_rows: int = 0, tuning_file: str | None = None,
+                 overlap: bool = False):
         torch = _torch()
         self.lib = _lib.load()
         self.device = torch.cuda.current_device()
@@ -84,6 +87,7 @@ class Inpainter:
         opt.search_alpha = float(alpha)
         opt.loop_mode = LOOPS[loop]
         opt.tile_rows = int(tile_rows)
+        opt.search_variant = 1 if overlap else 0
         self._tf = tuning_file.encode() if tuning_file else None
         opt.tuning_file = self._tf
         if self._alloc is not None:

@@ -122,9 +122,11 @@ bool alloc_n(inpaint_ctx* c, T*& p, size_t n) {
   return p != nullptr;
 }
 
-void search_rect(const uint8_t* mask, int mstride, int W, int H, int r, double alpha,
+void search_rect(const uint8_t* mask, int mstride, int W, int H, int r, double alpha, bool overlap,
                  int* x0o, int* x1o, int* y0o, int* y1o) {
-  int lo_x = r, hi_x = W - 1 - r, lo_y = r, hi_y = H - 1 - r;
+  // every interior centre; the partial-overlap variant admits border centres too
+  int lo_x = overlap ? 0 : r, hi_x = overlap ? W - 1 : W - 1 - r;
+  int lo_y = overlap ? 0 : r, hi_y = overlap ? H - 1 : H - 1 - r;
   if (alpha >= 0.0 && mask) {
     int bx0 = W, bx1 = -1, by0 = H, by1 = -1;
     for (int y = 0; y < H; ++y)
@@ -189,7 +191,9 @@ int launch_iteration(inpaint_ctx* c, int use_cond) {
 }
 
 bool use_engine(const inpaint_ctx* c) {
-  if (c->opt.loop_mode == INPAINT_LOOP_GRAPH || c->opt.form == INPAINT_FORM_TC) return false;
+  if (c->opt.loop_mode == INPAINT_LOOP_GRAPH || c->opt.form == INPAINT_FORM_TC ||
+      c->opt.search_variant != INPAINT_SEARCH_FULL)
+    return false;
   return c->r <= 8;
 }
 
@@ -358,6 +362,13 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
     g_last_error = "the tensor-core form supports patch_radius <= 8 in the graph loop";
     return INPAINT_ERR_UNSUPPORTED;
   }
+  if (o.search_variant != INPAINT_SEARCH_FULL && o.search_variant != INPAINT_SEARCH_OVERLAP)
+    return INPAINT_ERR_ARG;
+  if (o.search_variant == INPAINT_SEARCH_OVERLAP &&
+      (o.form != INPAINT_FORM_PLAIN || r > 8 || o.loop_mode == INPAINT_LOOP_ENGINE)) {
+    g_last_error = "the partial-overlap search is the plain form, patch_radius <= 8, graph loop";
+    return INPAINT_ERR_UNSUPPORTED;
+  }
 
   inpaint_ctx* c = new (std::nothrow) inpaint_ctx();
   if (!c) return INPAINT_ERR_NOMEM;
@@ -384,7 +395,9 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
   s.W = W;
   s.H = H;
   s.r = r;
-  search_rect(mask, mask_stride, W, H, r, o.search_alpha, &s.cx0, &s.cx1, &s.cy0, &s.cy1);
+  search_rect(mask, mask_stride, W, H, r, o.search_alpha, o.search_variant == INPAINT_SEARCH_OVERLAP,
+              &s.cx0, &s.cx1, &s.cy0, &s.cy1);
+  s.overlap = o.search_variant == INPAINT_SEARCH_OVERLAP ? 1 : 0;
   s.pitch = (W + 3) & ~3;
   s.t0x = (W + kT0 - 1) / kT0;
   s.t0y = (H + kT0 - 1) / kT0;
@@ -1129,6 +1142,10 @@ int batch_create_impl(const inpaint_image* images, int n, const inpaint_options*
   };
   inpaint_options_default(&b->opt);
   if (opt) b->opt = *opt;
+  if (b->opt.search_variant != INPAINT_SEARCH_FULL) {
+    g_last_error = "batches run the persistent engine: full search only";
+    return fail(INPAINT_ERR_UNSUPPORTED);
+  }
   if (b->opt.form != INPAINT_FORM_PLAIN) {
     g_last_error = "the batched form runs the plain search";
     return fail(INPAINT_ERR_UNSUPPORTED);
@@ -1412,6 +1429,11 @@ int inpaint_server_create(size_t hbm_budget_bytes, int max_slots, int iters_per_
   if (!s) return INPAINT_ERR_NOMEM;
   inpaint_options_default(&s->opt);
   if (opt) s->opt = *opt;
+  if (s->opt.search_variant != INPAINT_SEARCH_FULL) {
+    delete s;
+    g_last_error = "the server runs the persistent engine: full search only";
+    return INPAINT_ERR_UNSUPPORTED;
+  }
   s->opt.form = INPAINT_FORM_PLAIN;
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;

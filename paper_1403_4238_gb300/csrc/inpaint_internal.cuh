@@ -61,7 +61,7 @@ struct Ctrl {
   int px, py;      // target centre selected for the next iteration (-1: none)
   int n_valid;     // valid candidate centres inside the search rectangle
   int iter_limit;  // kernels do nothing once iter reaches this
-  int pad0;
+  int n_adm;       // partial-overlap search: admissible candidates of the current search
   double prio;     // P(p^) of the selected target
   double conf;     // C(p^) of the selected target
   unsigned long long evals;  // sum over iterations of n_cand * n_known
@@ -117,6 +117,7 @@ struct ImgState {
   int trace_cap;
   int srw;                 // engine search rows per warp (1 or 2)
   int n_partial;           // search CTAs writing partial[]
+  int overlap;             // 1: partial-overlap search variant (Alg. 1, Sec. 5.4)
   uint32_t* img;
   uint8_t* omega;
   uint8_t* gray;

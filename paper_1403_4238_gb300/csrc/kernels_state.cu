@@ -115,7 +115,7 @@ __global__ void k_ctrl_init(Ctrl* c) {
   c->py = -1;
   c->n_valid = 0;
   c->iter_limit = 0x7fffffff;
-  c->pad0 = 0;
+  c->n_adm = 0;
   c->prio = 0.0;
   c->conf = 0.0;
   c->evals = 0ull;

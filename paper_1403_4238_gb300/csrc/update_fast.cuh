@@ -483,7 +483,9 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const int W = s.W, H = s.H;
   const int px = __ldcg(&c->px), py = __ldcg(&c->py);
   const double cp = __ldcg(&c->conf), pp = __ldcg(&c->prio);
-  const int n_cand = __ldcg(&c->n_valid), it = __ldcg(&c->iter);
+  // candidates of this iteration's search: the validity-count total, or the
+  // admissible ones the partial-overlap search counted
+  const int n_cand = s.overlap ? __ldcg(&c->n_adm) : __ldcg(&c->n_valid), it = __ldcg(&c->iter);
   int remaining = __ldcg(&c->remaining);
 
   // best source key
@@ -741,6 +743,7 @@ __device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm, bool cp_s
     c->remaining = sm.remaining;
     c->iter = sm.it + 1;
     c->n_valid = sm.n_cand + sm.newly;
+    if (s.overlap) c->n_adm = 0;  // the next search counts afresh
     atomicAdd(&c->evals, (unsigned long long)sm.n_cand * (unsigned long long)sm.n_known);
     if (!next) {
       c->px = -1;

@@ -40,7 +40,27 @@ def test_status_strings_without_gpu():
         assert lib.inpaint_status_str(code)
     opt = _lib.Options()
     lib.inpaint_options_default(ctypes.byref(opt))
-    assert opt.form == 0 and opt.search_alpha < 0
+    assert opt.form == 0 and opt.search_alpha < 0 and opt.search_variant == 0
+
+
+def test_search_variant_options_checked_before_any_device_work():
+    lib = _lib.load()
+    ctx = ctypes.c_void_p()
+    buf = (ctypes.c_uint8 * (3 * 30 * 30))()
+
+    def create(r, **fields):
+        opt = _lib.Options()
+        lib.inpaint_options_default(ctypes.byref(opt))
+        for k, v in fields.items():
+            setattr(opt, k, v)
+        return lib.inpaint_create(buf, 30, 30, 90, buf, 30, r, ctypes.byref(opt), ctypes.byref(ctx))
+
+    assert create(2, search_variant=5) == -1
+    # the partial-overlap variant: plain form, radius <= 8, graph loop only
+    assert create(2, search_variant=1, form=1) == -6
+    assert create(9, search_variant=1) == -6
+    assert create(2, search_variant=1, loop_mode=1) == -6
+    assert not ctx.value
 
 
 def test_bad_arguments_rejected_before_any_device_work():
