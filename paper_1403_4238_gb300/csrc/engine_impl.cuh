@@ -647,8 +647,8 @@ __global__ void __launch_bounds__(kEngThreads) k_update_fast(ImgState s, cudaGra
     return;
   }
   spec_phase<R>(s, usm, uca, false);
-  const bool ok = update_phase<R>(s, s.partial, s.n_partial, usm, uca);
-  if (ok) update_finish<R>(s, usm, false);
+  const bool ok = update_phase<R>(s, s.partial, s.n_partial, usm, uca, -1, s.overlap != 0);
+  if (ok) update_finish<R>(s, usm, false, s.overlap != 0);
   if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, ok && loop_active(s.ctrl) ? 1u : 0u);
 }
 

@@ -472,10 +472,12 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
 // patch or the state is inconsistent.  Whole block; ends with a __syncthreads.
 // Thread `fence_thread` (if any) issues a gpu-scope fence once the pixel,
 // mask and count writes of the iteration are issued (see the engine's
-// publication).
+// publication).  `overlap_counts`: the search was the partial-overlap variant,
+// whose admissible candidates it counted in ctrl->n_adm.
 template <int R>
 __device__ bool update_phase(const ImgState& s, const unsigned long long* partial, int n_partial,
-                             UpdSmem<R>& sm, UpdCache<R>& ca, int fence_thread = -1) {
+                             UpdSmem<R>& sm, UpdCache<R>& ca, int fence_thread = -1,
+                             bool overlap_counts = false) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW, NC = G::NC;
   Ctrl* c = s.ctrl;
@@ -485,7 +487,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const double cp = __ldcg(&c->conf), pp = __ldcg(&c->prio);
   // candidates of this iteration's search: the validity-count total, or the
   // admissible ones the partial-overlap search counted
-  const int n_cand = s.overlap ? __ldcg(&c->n_adm) : __ldcg(&c->n_valid), it = __ldcg(&c->iter);
+  const int n_cand = overlap_counts ? __ldcg(&c->n_adm) : __ldcg(&c->n_valid), it = __ldcg(&c->iter);
   int remaining = __ldcg(&c->remaining);
 
   // best source key
@@ -719,7 +721,8 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
 // persistent engine publishes the next target to its searchers first.
 // Whole block; ends with a __syncthreads.
 template <int R>
-__device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm, bool cp_staged) {
+__device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm, bool cp_staged,
+                              bool overlap_counts = false) {
   Ctrl* c = s.ctrl;
   const bool next = sm.remaining > 0 && sm.next_key != 0ull;
   if (threadIdx.x == 0) {
@@ -743,7 +746,7 @@ __device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm, bool cp_s
     c->remaining = sm.remaining;
     c->iter = sm.it + 1;
     c->n_valid = sm.n_cand + sm.newly;
-    if (s.overlap) c->n_adm = 0;  // the next search counts afresh
+    if (overlap_counts) c->n_adm = 0;  // the next search counts afresh
     atomicAdd(&c->evals, (unsigned long long)sm.n_cand * (unsigned long long)sm.n_known);
     if (!next) {
       c->px = -1;
