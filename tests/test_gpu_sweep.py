@@ -40,3 +40,19 @@ def test_table3_case_matches_oracle(api, name, r, alpha):
         for f in ("px", "py", "qx", "qy", "ssd"):
             assert [t[f] for t in tr] == [int(t[f]) for t in ora.trace], f
         assert np.array_equal(ip.result(), ora.rgb)
+
+
+def test_sweep_runs_and_tabulates(api):
+    from paper_1403_4238_gb300 import sweep
+
+    rows = sweep.sweep(names=["river"], radii=(4, 6), alphas=(0.5, -1.0), log=lambda *a: None)
+    assert len(rows) == 4 and all(r["status"] == "ok" for r in rows)
+    by = {(r["P"], r["alpha"]): r for r in rows}
+    # a smaller search area never does more work
+    for P in (9, 13):
+        assert 0 < by[(P, 0.5)]["evals"] <= by[(P, -1.0)]["evals"]
+    # the exact work of one point equals the oracle's
+    case = synth.table3_case("river", 4)
+    assert by[(9, 0.5)]["evals"] == oracle.run(case.rgb, case.mask, 4, alpha=0.5).evals
+    md = sweep.table(rows)
+    assert md.count("| river |") == 2
