@@ -214,12 +214,15 @@ __device__ inline void stage_isophotes(UpdSmem<R>& sm) {
   for (int i = threadIdx.x; i < NS * NS; i += blockDim.x) {
     const int lx = i % NS, ly = i / NS;
     int m = -1, g = 0;
-    if (lx >= 1 && lx < NS - 1 && ly >= 1 && ly < NS - 1 && sm.om[i] == 0 && sm.om[i - 1] == 0 &&
-        sm.om[i + 1] == 0 && sm.om[i - NS] == 0 && sm.om[i + NS] == 0) {
+    if (lx >= 1 && lx < NS - 1 && ly >= 1 && ly < NS - 1) {
+      // all nine reads issued together (no short-circuit chain of loads)
+      const int o = sm.om[i] | sm.om[i - 1] | sm.om[i + 1] | sm.om[i - NS] | sm.om[i + NS];
       const int gx = (int)sm.gr[i + 1] - (int)sm.gr[i - 1];
       const int gy = (int)sm.gr[i + NS] - (int)sm.gr[i - NS];
-      m = gx * gx + gy * gy;
-      g = ((gx + 512) << 16) | (gy + 512);
+      if (o == 0) {
+        m = gx * gx + gy * gy;
+        g = ((gx + 512) << 16) | (gy + 512);
+      }
     }
     sm.mag[i] = m;
     sm.gxy[i] = g;
@@ -227,7 +230,9 @@ __device__ inline void stage_isophotes(UpdSmem<R>& sm) {
 }
 
 __device__ inline bool front_local(const uint8_t* om, int l, int NS) {
-  return om[l] == 1 && (om[l - 1] == 0 || om[l + 1] == 0 || om[l - NS] == 0 || om[l + NS] == 0);
+  // the five reads are independent (no short-circuit chain of loads)
+  const int c = om[l], a = om[l - 1], b = om[l + 1], u = om[l - NS], d = om[l + NS];
+  return c == 1 && (a == 0 || b == 0 || u == 0 || d == 0);
 }
 
 // Initial priorities, one CTA per NW x NW window of the image (direct
