@@ -295,8 +295,9 @@ def batch_section(api, flush, steps, log):
     from paper_1403_4238_gb300 import autotune, synth
 
     cases = synth.batch_cases(64)
-    tf = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                      "tuning_bench.txt")
+    import tempfile
+
+    tf = os.path.join(tempfile.mkdtemp(prefix="inpaint_tune_"), "tuning_bench.txt")
     table = autotune.tune((4, 5), log=lambda *a: None)
     autotune.write(table, tf)
     items = [(c.rgb, c.mask, c.r) for c in cases]
