@@ -262,6 +262,44 @@ def tc_section(api, case, flush, steps, peaks, plain_ms=None, plain_out=None):
     return out
 
 
+# Initialisation (row a1), algorithmic bytes per pixel: the RGB + mask input
+# read (4) and the state written: RGBA word 4, mask 1, grey 1, confidence 8,
+# validity count 4, priority key 8, confidence of the last evaluation 8.
+INIT_BYTES_PER_PX = 4 + 4 + 1 + 1 + 8 + 4 + 8 + 8
+
+
+def init_section(api, cases, flush, reps, hbm_gbs):
+    """Initialisation from device inputs (inpaint_reset: unpack, integral
+    image, validity counts, priorities, tiles, first selection) against the
+    HBM bandwidth its algorithmic bytes would need."""
+    import torch
+
+    out = []
+    for case in cases:
+        drgb = torch.from_numpy(case.rgb).cuda()
+        dmask = torch.from_numpy(case.mask).cuda()
+        with api.Inpainter(case.rgb, case.mask, case.r, loop="engine") as ip:
+            ip.reset(drgb, dmask)
+            ts = []
+            for _ in range(reps):
+                l2_flush(flush)
+                torch.cuda.synchronize()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record(ip.stream)
+                ip.reset(drgb, dmask)
+                ev[1].record(ip.stream)
+                ev[1].synchronize()
+                ts.append(ev[0].elapsed_time(ev[1]))
+        H, W = case.mask.shape
+        ms = statistics.mean(ts)
+        gbs = INIT_BYTES_PER_PX * W * H / (ms * 1e-3) / 1e9
+        out.append({"workload": f"{W}x{H}", "us": 1e3 * ms, "bytes": INIT_BYTES_PER_PX * W * H,
+                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+                                 "frac": gbs / hbm_gbs if hbm_gbs else None,
+                                 "note": "a chain of small kernels: latency-bound at these sizes"}})
+    return out
+
+
 def overlap_section(api, case, flush, steps, peak_evals):
     """Partial-overlap search variant (Algorithm 1, Sec. 5.4) against the full
     search, both in the graph loop: whole removal, exact work, and the search
@@ -475,8 +513,10 @@ def main():
             from paper_1403_4238_gb300 import synth
 
             line["tc"] = tc_section(api, case, flush, 3, peaks, line["ms_per_removal"], plain_out)
-            line["tc_hd"] = tc_section(api, synth.hd_blob(), flush, 2, peaks)
+            hd = synth.hd_blob()
+            line["tc_hd"] = tc_section(api, hd, flush, 2, peaks)
             line["overlap"] = overlap_section(api, case, flush, 3, line["roofline"]["peak"])
+            line["init"] = init_section(api, [case, hd], flush, 5, peaks.get("hbm_gbs"))
             line["batched"] = batch_section(api, flush, 3, print)
             line["serving"] = serving_section(api, args.serve_requests)
         if not args.no_cpu_baseline and world == 1:

@@ -55,6 +55,7 @@ LOOPS = ["engine", "graph"]
 @pytest.mark.parametrize("W,H,r,seed", [
     (20, 16, 1, 1), (24, 20, 2, 2), (33, 27, 3, 3), (40, 31, 4, 4), (47, 35, 5, 5),
     (52, 45, 6, 6), (61, 50, 7, 7), (70, 58, 8, 8), (75, 64, 9, 9), (90, 80, 12, 10),
+    (240, 160, 32, 14),  # the largest radius (65 x 65 patches)
 ])
 def test_tiny_full_runs_every_radius(api, W, H, r, seed, loop):
     if loop == "engine" and r > 8:
