@@ -44,7 +44,9 @@ typedef enum {
   INPAINT_ERR_ARG = -1,          /* invalid argument (sizes, radius, pointers, no known pixel) */
   INPAINT_ERR_NOMEM = -2,        /* a device or pinned-host allocation failed */
   INPAINT_ERR_CUDA = -3,         /* a CUDA runtime call failed */
-  INPAINT_ERR_NO_SOURCE = -4,    /* no fully-known source patch exists; state unchanged */
+  INPAINT_ERR_NO_SOURCE = -4,    /* no admissible source patch (fully known; with the partial-
+                                    overlap search: known under every pixel to fill); state
+                                    unchanged */
   INPAINT_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
   INPAINT_ERR_UNSUPPORTED = -6,  /* valid request this build or device cannot serve */
   INPAINT_ERR_INTERNAL = -7      /* a self-check (debug_checks) found inconsistent state */
