@@ -162,6 +162,7 @@ SIGNATURES = {
     "inpaint_probe_peaks": (_I, [ctypes.POINTER(Peaks)]),
     "inpaint_time_search": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "inpaint_run_withheld": (_I, [_P, _I, ctypes.c_double, _I, ctypes.POINTER(_I)]),
     "inpaint_best_patch_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "inpaint_batch_create": (_I, [ctypes.POINTER(Image), _I, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "inpaint_batch_reset": (_I, [_P]),

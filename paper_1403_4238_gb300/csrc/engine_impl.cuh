@@ -602,7 +602,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       const unsigned long long best = search_round(px, py);
       if (tid == 0) {
         tpart[rank] = best;
-        red_release_add(&tc->arrive, 1u);
+        if (rank + 1 != ea.withhold) red_release_add(&tc->arrive, 1u);
       }
     }
     // searchers and idle CTAs: wait for the next round

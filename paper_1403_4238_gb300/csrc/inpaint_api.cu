@@ -698,6 +698,22 @@ int inpaint_time_search(inpaint_ctx* c, int form, int reps, double* ms_per_searc
   return INPAINT_OK;
 }
 
+int inpaint_run_withheld(inpaint_ctx* c, int rank, double wait_limit_s, int max_iters,
+                         int* iters_done) {
+  if (iters_done) *iters_done = 0;
+  if (!c || rank < 0 || !(wait_limit_s > 0.0) || wait_limit_s > 10.0) return INPAINT_ERR_ARG;
+  if (!use_engine(c)) return INPAINT_ERR_UNSUPPORTED;
+  int rc = setup_engine(c);
+  if (rc) return rc;
+  const unsigned long long limit0 = c->ea.wait_limit_ns;
+  c->ea.wait_limit_ns = (unsigned long long)(wait_limit_s * 1e9);
+  c->ea.withhold = rank + 1;
+  rc = inpaint_run(c, max_iters, iters_done, nullptr, 0);
+  c->ea.wait_limit_ns = limit0;
+  c->ea.withhold = 0;
+  return rc;
+}
+
 int inpaint_loop_timing(const inpaint_ctx* c, uint64_t* search_ns, uint64_t* update_ns,
                         int* iters) {
   if (!c) return INPAINT_ERR_ARG;

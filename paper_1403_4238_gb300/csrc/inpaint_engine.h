@@ -32,6 +32,8 @@ struct EngineArgs {
   unsigned long long wait_limit_ns;
   unsigned long long tick_ns;  // > 0: teams stop between iterations once the launch
                                // has run this long (serving ticks); 0: run to the end
+  int withhold;                // failure injection: > 0 makes searcher rank withhold - 1
+                               // of every team skip its arrival; 0 normally
 };
 
 // Per-CTA engine state carried from one image of a team's list to the next.

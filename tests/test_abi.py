@@ -74,3 +74,8 @@ def test_bad_arguments_rejected_before_any_device_work():
     assert lib.inpaint_create(None, 10, 10, 30, buf, 10, 1, None, ctypes.byref(ctx)) == -1
     assert lib.inpaint_create(buf, 10, 10, 20, buf, 10, 1, None, ctypes.byref(ctx)) == -1
     assert not ctx.value
+    # failure injection: null context or an out-of-range wait limit
+    done = ctypes.c_int(7)
+    assert lib.inpaint_run_withheld(None, 0, 0.05, 0, ctypes.byref(done)) == -1 and done.value == 0
+    assert lib.inpaint_run_withheld(None, -1, 0.05, 0, None) == -1
+    assert lib.inpaint_run_withheld(None, 0, 0.0, 0, None) == -1
