@@ -157,6 +157,36 @@ int inpaint_reset(inpaint_ctx* ctx, const uint8_t* rgb, int rgb_stride_bytes,
  * receives the iteration's record.  Synchronises the context's stream. */
 int inpaint_step(inpaint_ctx* ctx, inpaint_step_info* info);
 
+/* One fill iteration split over candidate rows, for a removal sharded over
+ * several GPUs (each holding an identical replica of the context): every
+ * shard searches its rows, the packed keys are reduced to their minimum,
+ * and every replica applies that one key.  findBestPatch (Sec. 3, Eq. 3-4)
+ * is a minimum over candidate centres, so the minimum of the rows' minima is
+ * the full search's result (ties: lowest linear index, as the packed key
+ * orders them), and replicas that apply the same keys stay identical.  Plain
+ * form, exhaustive or alpha-limited search (not the tensor-core form or the
+ * partial-overlap variant: INPAINT_ERR_UNSUPPORTED).
+ *
+ * inpaint_search_rows: searches the candidate centres of image rows
+ * [y0, y1) (clipped to the search rectangle) for the current target p^ and
+ * writes the smallest packed key (SSD << 32 | y * W + x) to *key_out (host
+ * pointer), or INPAINT_KEY_NONE when those rows hold no candidate.  The state
+ * does not change.  Returns INPAINT_OK, INPAINT_DONE (Omega empty) or an
+ * error (INPAINT_ERR_ARG: null pointers or y0 > y1).  Synchronises the
+ * context's stream.
+ *
+ * inpaint_apply_key: completes the iteration with `key` (the minimum over
+ * all row ranges of the whole search rectangle): copy, confidence, mask,
+ * validity counts, priorities, next p^, exactly as inpaint_step does, and
+ * info (nullable) receives its record.  INPAINT_KEY_NONE means no source was
+ * found anywhere: INPAINT_ERR_NO_SOURCE, state unchanged.  A key whose centre
+ * is not an interior pixel (patch inside the image) is rejected with
+ * INPAINT_ERR_ARG; any other key must come from inpaint_search_rows on a
+ * replica in the same state.  Synchronises the context's stream. */
+#define INPAINT_KEY_NONE 0xffffffffffffffffull
+int inpaint_search_rows(inpaint_ctx* ctx, int y0, int y1, unsigned long long* key_out);
+int inpaint_apply_key(inpaint_ctx* ctx, unsigned long long key, inpaint_step_info* info);
+
 /* Runs iterations on the device until Omega is empty, an error occurs, or
  * max_iters iterations (<= 0: no limit) have run, with no host round trip
  * per iteration.  *iters_done (nullable) receives the number of iterations

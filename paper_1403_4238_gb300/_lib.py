@@ -118,6 +118,8 @@ STEP_DTYPE = np.dtype(
 )
 assert STEP_DTYPE.itemsize == ctypes.sizeof(StepInfo)
 
+KEY_NONE = (1 << 64) - 1  # INPAINT_KEY_NONE: no candidate in the searched rows
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -162,6 +164,8 @@ SIGNATURES = {
     "inpaint_probe_peaks": (_I, [ctypes.POINTER(Peaks)]),
     "inpaint_time_search": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "inpaint_search_rows": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_uint64)]),
+    "inpaint_apply_key": (_I, [_P, ctypes.c_uint64, _P]),
     "inpaint_run_withheld": (_I, [_P, _I, ctypes.c_double, _I, ctypes.POINTER(_I)]),
     "inpaint_best_patch_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "inpaint_batch_create": (_I, [ctypes.POINTER(Image), _I, ctypes.POINTER(Options), ctypes.POINTER(_P)]),

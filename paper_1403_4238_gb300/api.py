@@ -209,6 +209,28 @@ class Inpainter:
                "inpaint_search_rect")
         return tuple(x.value for x in v)
 
+    # -- row-sharded iterations (one removal over several replicas) -------
+    def search_rows(self, y0: int, y1: int):
+        """Smallest packed key (SSD << 32 | y*W + x) among the candidate
+        centres of rows [y0, y1) for the current target; _lib.KEY_NONE if
+        those rows hold none; None once the removal is done."""
+        key = ctypes.c_uint64()
+        rc = _check(self.lib.inpaint_search_rows(self.ctx, int(y0), int(y1), ctypes.byref(key)),
+                    "inpaint_search_rows")
+        return None if rc == 1 else key.value
+
+    def apply_key(self, key: int):
+        """Complete the iteration with the global minimum key; returns its
+        record (None if the removal was already done)."""
+        info = StepInfo()
+        rc = _check(self.lib.inpaint_apply_key(self.ctx, ctypes.c_uint64(int(key)), ctypes.byref(info)),
+                    "inpaint_apply_key")
+        if rc == 1:
+            return None
+        out = np.zeros(1, STEP_DTYPE)
+        ctypes.memmove(out.ctypes.data, ctypes.byref(info), STEP_DTYPE.itemsize)
+        return out[0]
+
 
 def remove_object(rgb, mask, r: int, **kw):
     """Convenience: create, run to completion, return (rgb_out, trace)."""

@@ -78,6 +78,7 @@ struct inpaint_ctx {
   unsigned long long* d_epart = nullptr;
   int* d_err = nullptr;
   int* h_err = nullptr;
+  unsigned long long* d_key = nullptr;  // key applied by inpaint_apply_key
 
   void* dalloc(size_t bytes) {
     void* p = nullptr;
@@ -695,6 +696,77 @@ int inpaint_time_search(inpaint_ctx* c, int form, int reps, double* ms_per_searc
   *ms_per_search = (double)ms / reps;
   if (best_key) *best_key = *std::min_element(keys.begin(), keys.end());
   if (evals) *evals = (unsigned long long)n_known * (unsigned long long)std::max(h.n_valid, 0);
+  return INPAINT_OK;
+}
+
+namespace {
+
+// Sharded iterations run the plain form's search and update kernels on the
+// full search (the variant counts its admissible candidates in the search).
+int sharded_ok(const inpaint_ctx* c) {
+  if (c->opt.form != INPAINT_FORM_PLAIN || c->opt.search_variant != INPAINT_SEARCH_FULL) {
+    g_last_error = "row-sharded iterations need the plain form and the full search";
+    return INPAINT_ERR_UNSUPPORTED;
+  }
+  return INPAINT_OK;
+}
+
+}  // namespace
+
+int inpaint_search_rows(inpaint_ctx* c, int y0, int y1, unsigned long long* key_out) {
+  if (!c || !key_out || y0 > y1) return INPAINT_ERR_ARG;
+  *key_out = INPAINT_KEY_NONE;
+  int rc = sharded_ok(c);
+  if (rc) return rc;
+  if ((rc = read_ctrl(c))) return rc;
+  if (c->h_ctrl->status != 0) return c->h_ctrl->status;
+  if (c->h_ctrl->remaining == 0) return INPAINT_DONE;
+  ImgState s = c->st;
+  s.cy0 = std::max(s.cy0, y0);
+  s.cy1 = std::min(s.cy1, y1 - 1);
+  if (s.cy0 > s.cy1 || s.cx0 > s.cx1) return INPAINT_OK;
+  const dim3 g = search_plain_grid(s);
+  s.n_partial = (int)(g.x * g.y);  // fewer rows: at most the full rectangle's grid
+  if (s.n_partial <= 0 || s.n_partial > c->st.n_partial) return INPAINT_ERR_INTERNAL;
+  CK(prepare_search_plain(s.r));
+  CK(launch_search_plain(s, c->stream));
+  std::vector<unsigned long long> keys(s.n_partial);
+  CK(cudaMemcpyAsync(keys.data(), s.partial, sizeof(unsigned long long) * keys.size(),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *key_out = *std::min_element(keys.begin(), keys.end());
+  return INPAINT_OK;
+}
+
+int inpaint_apply_key(inpaint_ctx* c, unsigned long long key, inpaint_step_info* info) {
+  if (!c) return INPAINT_ERR_ARG;
+  int rc = sharded_ok(c);
+  if (rc) return rc;
+  if (key != INPAINT_KEY_NONE) {
+    const unsigned long long q = key & 0xffffffffull;
+    const long long qx = (long long)(q % (unsigned long long)c->W), qy = (long long)(q / (unsigned long long)c->W);
+    if (qy >= c->H || qx < c->r || qx > c->W - 1 - c->r || qy < c->r || qy > c->H - 1 - c->r) {
+      g_last_error = "the key's centre is not an interior pixel";
+      return INPAINT_ERR_ARG;
+    }
+  }
+  if ((rc = read_ctrl(c))) return rc;
+  if (c->h_ctrl->status != 0) return c->h_ctrl->status;
+  if (c->h_ctrl->remaining == 0) return INPAINT_DONE;
+  if (!c->d_key && !alloc_n(c, c->d_key, 1)) return INPAINT_ERR_NOMEM;
+  if ((rc = set_limit(c, INT_MAX))) return rc;
+  CK(cudaMemcpyAsync(c->d_key, &key, sizeof(key), cudaMemcpyHostToDevice, c->stream));
+  ImgState s = c->st;
+  s.partial = c->d_key;
+  s.n_partial = 1;
+  if (c->r <= 8)
+    CK(launch_update_fast(s, c->cond, 0, c->stream));
+  else
+    CK(launch_update(s, 1, c->cond, 0, c->stream));
+  if (c->opt.debug_checks) CK(launch_verify_count(c->st, c->stream));
+  if ((rc = read_ctrl(c))) return rc;
+  if (c->h_ctrl->status != 0) return c->h_ctrl->status;
+  if (info) *info = c->h_ctrl->last;
   return INPAINT_OK;
 }
 

@@ -79,3 +79,6 @@ def test_bad_arguments_rejected_before_any_device_work():
     assert lib.inpaint_run_withheld(None, 0, 0.05, 0, ctypes.byref(done)) == -1 and done.value == 0
     assert lib.inpaint_run_withheld(None, -1, 0.05, 0, None) == -1
     assert lib.inpaint_run_withheld(None, 0, 0.0, 0, None) == -1
+    key = ctypes.c_uint64(5)
+    assert lib.inpaint_search_rows(None, 0, 10, ctypes.byref(key)) == -1
+    assert lib.inpaint_apply_key(None, 0, None) == -1

@@ -62,3 +62,98 @@ def test_two_gloo_ranks_agree_on_split_and_max():
         assert sorted(i for part in got for i in part) == list(range(40))
         assert not set(got[0]) & set(got[1])
     assert res[0][1] == res[1][1]
+
+
+# -- one removal split over ranks by candidate rows ----------------------
+
+STEP_FIELDS = ("px", "py", "qx", "qy", "ssd", "filled", "remaining")
+
+
+def test_row_slabs_partition_the_rows():
+    for y0, y1 in ((4, 91), (4, 4), (10, 9)):
+        for world in (1, 2, 3, 5, 200):
+            slabs = pdist.row_slabs(y0, y1, world)
+            assert len(slabs) == world
+            rows = [y for lo, hi in slabs for y in range(lo, hi)]
+            assert rows == list(range(y0, y1 + 1))
+            sizes = [hi - lo for lo, hi in slabs]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def test_min_over_row_slabs_is_the_full_search():
+    """Replicas that search disjoint slabs and apply the minimum key follow
+    the oracle's own run, iteration by iteration (3 emulated ranks, one of
+    them with a slab that starts above the search rectangle)."""
+    import numpy as np
+
+    import oracle
+    from oracle_replica import OracleReplica
+    from paper_1403_4238_gb300 import synth
+
+    case = synth.small_rect(seed=71)
+    full = oracle.run(case.rgb, case.mask, case.r)
+    reps = [OracleReplica(case.rgb, case.mask, case.r) for _ in range(3)]
+    _, _, y0, y1 = reps[0].search_rect()
+    slabs = pdist.row_slabs(y0, y1, 3)
+    slabs[0] = (0, slabs[0][1])
+    recs = []
+    while True:
+        keys = [rep.search_rows(lo, hi) for rep, (lo, hi) in zip(reps, slabs)]
+        if keys[0] is None:
+            assert all(k is None for k in keys)
+            break
+        g = min(keys)
+        out = [rep.apply_key(g) for rep in reps]
+        assert all(o[f] == out[0][f] for o in out for f in STEP_FIELDS)
+        recs.append(out[0])
+    assert len(recs) == full.iters
+    for a, b in zip(recs, full.trace):
+        assert all(a[f] == b[f] for f in STEP_FIELDS)
+    for rep in reps:
+        assert np.array_equal(rep.rgb, full.rgb)
+
+
+def _sharded_worker(rank, world, port, q):
+    import sys
+
+    import torch.distributed as dist
+
+    sys.path.insert(0, os.path.dirname(__file__))
+    from oracle_replica import OracleReplica
+    from paper_1403_4238_gb300 import synth
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        case = synth.small_rect(seed=72)
+        rep = OracleReplica(case.rgb, case.mask, case.r)
+        recs = pdist.run_row_sharded(rep)
+        q.put((rank, [tuple(int(t[f]) for f in STEP_FIELDS) for t in recs], rep.rgb.tobytes()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_run_one_removal_row_sharded():
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    import oracle
+    from paper_1403_4238_gb300 import synth
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    case = synth.small_rect(seed=72)
+    full = oracle.run(case.rgb, case.mask, case.r)
+    want = [tuple(int(t[f]) for f in STEP_FIELDS) for t in full.trace]
+    for rank, recs, rgb in res:
+        assert recs == want
+        assert np.frombuffer(rgb, np.uint8).reshape(full.rgb.shape).tolist() == full.rgb.tolist()
