@@ -206,26 +206,52 @@ __device__ inline void stage_nbhd(const ImgState& s, int cx, int cy, UpdSmem<R>&
   }
 }
 
-// Isophote candidates of the staged neighbourhood: pixels whose four
-// neighbours are known, with their central-difference grey gradient.
+// Isophote candidate at local pixel (lx, ly): eligible when it and its four
+// neighbours are known, with its central-difference grey gradient.
+template <int R>
+__device__ inline void isophote_at(UpdSmem<R>& sm, int lx, int ly) {
+  constexpr int NS = UpdGeom<R>::NS;
+  const int i = ly * NS + lx;
+  int m = -1, g = 0;
+  if (lx >= 1 && lx < NS - 1 && ly >= 1 && ly < NS - 1) {
+    // all nine reads issued together (no short-circuit chain of loads)
+    const int o = sm.om[i] | sm.om[i - 1] | sm.om[i + 1] | sm.om[i - NS] | sm.om[i + NS];
+    const int gx = (int)sm.gr[i + 1] - (int)sm.gr[i - 1];
+    const int gy = (int)sm.gr[i + NS] - (int)sm.gr[i - NS];
+    if (o == 0) {
+      m = gx * gx + gy * gy;
+      g = ((gx + 512) << 16) | (gy + 512);
+    }
+  }
+  sm.mag[i] = m;
+  sm.gxy[i] = g;
+}
+
+// Isophote candidates of the whole staged neighbourhood.
 template <int R>
 __device__ inline void stage_isophotes(UpdSmem<R>& sm) {
   constexpr int NS = UpdGeom<R>::NS;
-  for (int i = threadIdx.x; i < NS * NS; i += blockDim.x) {
-    const int lx = i % NS, ly = i / NS;
-    int m = -1, g = 0;
-    if (lx >= 1 && lx < NS - 1 && ly >= 1 && ly < NS - 1) {
-      // all nine reads issued together (no short-circuit chain of loads)
-      const int o = sm.om[i] | sm.om[i - 1] | sm.om[i + 1] | sm.om[i - NS] | sm.om[i + NS];
-      const int gx = (int)sm.gr[i + 1] - (int)sm.gr[i - 1];
-      const int gy = (int)sm.gr[i + NS] - (int)sm.gr[i - NS];
-      if (o == 0) {
-        m = gx * gx + gy * gy;
-        g = ((gx + 512) << 16) | (gy + 512);
-      }
+  for (int i = threadIdx.x; i < NS * NS; i += blockDim.x) isophote_at<R>(sm, i % NS, i / NS);
+}
+
+// Isophote candidates of part of the neighbourhood of p^.  The fill of the
+// iteration changes grey levels and the mask only inside Psi_p^, so a
+// candidate can change only within one pixel of it: in the box of
+// Chebyshev radius R + 1 around p^.  kRing false: every candidate outside
+// that box (the speculative phase, before the search ends, threads
+// [first, blockDim.x)); kRing true: the box itself, from the copied pixels.
+template <int R, bool kRing>
+__device__ inline void stage_isophotes_part(UpdSmem<R>& sm, int first) {
+  constexpr int NS = UpdGeom<R>::NS, RB = UpdGeom<R>::RB, RR = R + 1, NB = 2 * RR + 1;
+  constexpr int n = kRing ? NB * NB : NS * NS;
+  if ((int)threadIdx.x < first) return;
+  for (int k = (int)threadIdx.x - first; k < n; k += (int)blockDim.x - first) {
+    if (kRing) {
+      isophote_at<R>(sm, RB - RR + k % NB, RB - RR + k / NB);
+    } else {
+      const int lx = k % NS, ly = k / NS;
+      if (abs(lx - RB) > RR || abs(ly - RB) > RR) isophote_at<R>(sm, lx, ly);
     }
-    sm.mag[i] = m;
-    sm.gxy[i] = g;
   }
 }
 
@@ -463,6 +489,7 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
   const int fsat_warp = spare ? nchain / 32 : 0;
   if ((int)(threadIdx.x >> 5) == fsat_warp) warp_fsat<R>(sm);
   update_prefetch<R>(s, ca, spare ? nchain + 32 : 0, px, py);
+  stage_isophotes_part<R, false>(sm, spare ? nchain + 32 : 0);
   if (threadIdx.x == 0) {
     sm.nfront = nfront;
     sm.spec_iter = it;
@@ -537,16 +564,17 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const int ny_in = min(py + R, H - 1) - max(py - R, 0) + 1;
   const int n_known = nx_in * ny_in - filled;
 
-  // isophotes of the new grey levels, then for every window pixel the
+  // isophotes of the new grey levels (the ones the fill cannot change were
+  // computed by the speculative phase), then for every front pixel the
   // strongest one of its patch (first in row-major order on ties) as a
   // separable windowed maximum of keys (|grad|^2 + 1) << 12 | (4095 - l) over
-  // local indices l; the confidence array is free here and holds the keys
-  stage_isophotes<R>(sm);
+  // local indices l: rows here, columns in the priority loop below; the
+  // confidence array is free here and holds the row maxima
+  stage_isophotes_part<R, true>(sm, 0);
   __syncthreads();
   constexpr int HR = NW + 2 * R;  // rows of the horizontal pass
   uint32_t* hkey = reinterpret_cast<uint32_t*>(sm.cf);
-  uint32_t* wkey = hkey + HR * NW;
-  static_assert(sizeof(sm.cf) >= sizeof(uint32_t) * (HR * NW + NW * NW), "key scratch");
+  static_assert(sizeof(sm.cf) >= sizeof(uint32_t) * HR * NW, "key scratch");
   static_assert(NS * NS <= 4096, "local index fits in 12 bits");
   for (int i = tid; i < HR * NW; i += nt) {
     const int ly = RB - R2 - R + i / NW, lx = RB - R2 + i % NW;
@@ -559,17 +587,6 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       best = key > best ? key : best;
     }
     hkey[i] = best;
-  }
-  __syncthreads();
-  for (int i = tid; i < NW * NW; i += nt) {
-    const int wy = i / NW, wx = i % NW;
-    uint32_t best = 0u;
-#pragma unroll
-    for (int dy = 0; dy <= 2 * R; ++dy) {
-      const uint32_t key = hkey[(wy + dy) * NW + wx];
-      best = key > best ? key : best;
-    }
-    wkey[i] = best;
   }
   __syncthreads();
 
@@ -590,7 +607,12 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       const int i = sm.list[k];
       const int wx = i % NW - R2, wy = i / NW - R2;
       int gx, gy;
-      const uint32_t ik = wkey[i];
+      uint32_t ik = 0u;  // column maximum of the row maxima
+#pragma unroll
+      for (int dy = 0; dy <= 2 * R; ++dy) {
+        const uint32_t key = hkey[(i / NW + dy) * NW + i % NW];
+        ik = key > ik ? key : ik;
+      }
       gx = 0;
       gy = 0;
       if (ik) {
