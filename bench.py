@@ -177,8 +177,8 @@ EVALS_PER_CLK_SM = 64
 
 # DRAM bytes (read + write) of one k_engine launch on the headline workload,
 # from an ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum: 2.352 MB + 1.796 MB); None once the kernel changes.
-ENGINE_TRAFFIC_BYTES = 4148480
+# dram__bytes_write.sum: 2.350 MB + 2.198 MB); None once the kernel changes.
+ENGINE_TRAFFIC_BYTES = 4547840
 
 
 def measured_peaks():
