@@ -157,3 +157,39 @@ def test_two_gloo_ranks_run_one_removal_row_sharded():
     for rank, recs, rgb in res:
         assert recs == want
         assert np.frombuffer(rgb, np.uint8).reshape(full.rgb.shape).tolist() == full.rgb.tolist()
+
+
+def _minkey_worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        k = (32967075 << 32) | 5 if rank == 0 else (7 << 32) | 123456
+        got = [
+            pdist.min_key_over_ranks(k),                                      # both real
+            pdist.min_key_over_ranks(pdist.KEY_NONE if rank else (9 << 32)),  # one side has none
+            pdist.min_key_over_ranks(pdist.KEY_NONE),                         # nobody has one
+            pdist.min_key_over_ranks((3 << 32) | (10 + rank)),                # SSD tie: lower index
+        ]
+        q.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_min_key_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_minkey_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, got in res:
+        assert got == [(7 << 32) | 123456, 9 << 32, pdist.KEY_NONE, (3 << 32) | 10]
