@@ -47,7 +47,7 @@ WORKLOAD = "512x384 RGB, 3-ellipse mask 7.5-8.5%, r=4 (9x9), exhaustive search, 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=150,
@@ -78,6 +78,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def __enter__(self):
         try:
@@ -88,6 +89,13 @@ class ClockSampler:
             self.t.start()
         except OSError:
             self.proc = None
+            return self
+        # nvidia-smi takes a moment to start: wait (bounded) for its first
+        # sample so that the samples span the whole timed region
+        t0 = time.monotonic()
+        while not self.lines and self.proc.poll() is None and time.monotonic() - t0 < 3.0:
+            time.sleep(0.01)
+        self.first = len(self.lines)  # samples taken before the timed region
         return self
 
     def _read(self):
@@ -106,7 +114,8 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # the last sample before the region stands for its start
+        for ln in self.lines[max(0, self.first - 1):]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
