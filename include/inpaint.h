@@ -48,7 +48,7 @@ typedef enum {
                                     overlap search: known under every pixel to fill); state
                                     unchanged */
   INPAINT_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
-  INPAINT_ERR_UNSUPPORTED = -6,  /* valid request this build or device cannot serve */
+  INPAINT_ERR_UNSUPPORTED = -6,  /* valid request this library or device cannot serve */
   INPAINT_ERR_INTERNAL = -7      /* a self-check (debug_checks) found inconsistent state */
 } inpaint_status;
 

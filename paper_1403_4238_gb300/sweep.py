@@ -11,7 +11,7 @@ alpha, with the persistent engine, and each removal's time and exact
 algorithmic work (valid candidates x known target pixels, summed over the
 iterations) are reported next to Eq. 8's estimate.
 
-This build's candidates must lie fully in the known region (the reading of
+This library's candidates must lie fully in the known region (the reading of
 Eq. 3-4 used throughout), so a candidate that overlaps the object is not
 evaluated at all; in Eq. 8's terms that is k = 0.  Eq. 8 is printed for the
 paper's k = 0.5 and for k = 0.
