@@ -139,3 +139,31 @@ def test_batch_more_images_than_ctas_mixed_radii(api):
             out, iters, evals = b.result(i)
             assert iters == ref.iters and evals == ref.evals
             assert np.array_equal(out, ref.rgb), i
+
+
+def lattice_case(W=96, H=72, r=4, seed=21):
+    """Unknown pixels on a lattice of pitch 2r: every (2r+1)^2 patch holds
+    one, so no candidate is fully known and the first search finds none."""
+    rgb = synth.image(W, H, 5, 30.0, seed)
+    mask = np.zeros((H, W), np.uint8)
+    mask[r::2 * r, r::2 * r] = 1
+    return rgb, mask, r
+
+
+def test_batch_image_without_source_fails_alone(api):
+    cases = [(c.rgb, c.mask, c.r) for c in synth.batch_cases(4, seed=12)]
+    bad = lattice_case()
+    assert oracle.run(*bad).status == -4
+    cases.insert(2, bad)
+    solo = {}
+    for i, (rgb, mask, r) in enumerate(cases):
+        if i != 2:
+            with api.Inpainter(rgb, mask, r) as ip:
+                ip.run()
+                solo[i] = ip.result()
+    with api.Batch(cases) as b:
+        st = b.run()
+        assert st[2] == -4
+        for i in solo:
+            assert st[i] == 0, i
+            assert np.array_equal(b.result(i)[0], solo[i]), i

@@ -104,3 +104,23 @@ def test_time_budget_ticks_resume_long_requests(api):
             out, info = srv.poll(rid)
             assert info["status"] == 0
             assert np.array_equal(out, alone(api, *q))
+
+
+def test_request_without_source_fails_and_others_complete(api):
+    reqs = requests(5, 3)
+    W, H, r = 96, 72, 4
+    mask = np.zeros((H, W), np.uint8)
+    mask[r::2 * r, r::2 * r] = 1  # every (2r+1)^2 patch holds an unknown pixel: no source
+    reqs.insert(2, (synth.image(W, H, 5, 30.0, 31), mask, r))
+    with api.Server(hbm_budget_bytes=1 << 30, max_slots=4, iters_per_tick=8) as srv:
+        ids = [srv.submit(*q) for q in reqs]
+        srv.wait_idle(300)
+        st = srv.stats()
+        assert st["failed"] == 1 and st["completed"] == 5
+        for k, (rid, q) in enumerate(zip(ids, reqs)):
+            out, info = srv.poll(rid)
+            if k == 2:
+                assert info["status"] == -4
+                continue
+            assert info["status"] == 0
+            assert np.array_equal(out, alone(api, *q))
