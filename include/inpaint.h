@@ -298,7 +298,7 @@ int inpaint_batch_reset(inpaint_batch* b);
  * status (INPAINT_OK, INPAINT_DONE or an error).  Returns INPAINT_OK when
  * the launch ran (even if some images failed), else an error.
  * Synchronises the batch's stream. */
-int inpaint_batch_run(inpaint_batch* b, int max_iters, int* status_out);
+int inpaint_batch_run_ctx(inpaint_batch* b, int max_iters, int* status_out);
 
 /* Current image i (RGB, rows of stride_bytes) and its counters; any output
  * pointer may be NULL. */
@@ -312,6 +312,27 @@ int inpaint_batch_plan(const inpaint_batch* b, int* grid, int* n_teams, int* tea
 
 /* Releases everything (after synchronising the batch's stream). */
 void inpaint_batch_destroy(inpaint_batch* b);
+
+/* One-shot batched removal: n independent images, each W[i] x H[i] with
+ * patch radius r[i] (1..8), run to completion in one persistent launch
+ * (create, run, results, destroy of a batch object).  The fill loop of every
+ * image is the one of Sec. 3 (Eq. 1-4), bit for bit as inpaint_run on that
+ * image alone.
+ *   rgb[i]: host, dense W x H x 3 bytes; mask[i]: host, dense W x H bytes,
+ *           nonzero = remove.  Both are read only.
+ *   opt: NULL for defaults (opt->cuda_stream carries the work).
+ *   rgb_out[i]: host, dense W x H x 3 bytes, receives image i after its
+ *           removal (or the state where its loop stopped, see status_out).
+ *   status_out: nullable, n entries: INPAINT_OK, INPAINT_DONE (nothing to
+ *           remove) or the error that stopped image i (INPAINT_ERR_NO_SOURCE
+ *           for an image without an admissible source; the others still
+ *           finish).
+ * Returns INPAINT_OK when the launch ran, else the first error (a bad
+ * argument: INPAINT_ERR_ARG, with the index in inpaint_last_error()).
+ * Synchronous. */
+int inpaint_batch_run(int n, const uint8_t* const* rgb, const uint8_t* const* mask, const int* w,
+                      const int* h, const int* r, const inpaint_options* opt, uint8_t* const* rgb_out,
+                      int* status_out);
 
 /* ---- Serving loop: continuous batching of object-removal requests ----
  * A server owns a worker thread and a CUDA stream.  Submitted requests wait

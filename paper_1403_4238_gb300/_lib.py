@@ -170,7 +170,8 @@ SIGNATURES = {
     "inpaint_best_patch_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "inpaint_batch_create": (_I, [ctypes.POINTER(Image), _I, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "inpaint_batch_reset": (_I, [_P]),
-    "inpaint_batch_run": (_I, [_P, _I, _P]),
+    "inpaint_batch_run_ctx": (_I, [_P, _I, _P]),
+    "inpaint_batch_run": (_I, [_I, _P, _P, _P, _P, _P, ctypes.POINTER(Options), _P, _P]),
     "inpaint_batch_result": (_I, [_P, _I, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_uint64)]),
     "inpaint_batch_plan": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _P, _P]),
     "inpaint_batch_destroy": (None, [_P]),

@@ -312,7 +312,7 @@ class Batch:
 
     def run(self, max_iters: int = 0):
         st = (ctypes.c_int * self.n)()
-        _check(self.lib.inpaint_batch_run(self.b, int(max_iters), st), "inpaint_batch_run")
+        _check(self.lib.inpaint_batch_run_ctx(self.b, int(max_iters), st), "inpaint_batch_run_ctx")
         return list(st)
 
     def result(self, i: int):
@@ -331,6 +331,35 @@ class Batch:
         _check(self.lib.inpaint_batch_plan(self.b, ctypes.byref(g), ctypes.byref(t), team, size, rows),
                "inpaint_batch_plan")
         return dict(grid=g.value, teams=t.value, team=list(team), team_size=list(size), rows=list(rows))
+
+
+def batch_run(cases, *, tile_rows: int = 0, tuning_file: str | None = None, stream=None):
+    """One-shot batched removal (inpaint_batch_run): cases is a sequence of
+    (rgb (H, W, 3) uint8, mask (H, W), patch radius); returns (list of result
+    images, list of per-image statuses)."""
+    torch = _torch()
+    lib = _lib.load()
+    stream = stream if stream is not None else torch.cuda.Stream(torch.cuda.current_device())
+    opt = Options()
+    lib.inpaint_options_default(ctypes.byref(opt))
+    opt.cuda_stream = stream.cuda_stream
+    opt.tile_rows = int(tile_rows)
+    tf = tuning_file.encode() if tuning_file else None
+    opt.tuning_file = tf
+    rgbs, masks, outs = [], [], []
+    for rgb, mask, _ in cases:
+        m = np.ascontiguousarray(mask, np.uint8)
+        rgbs.append(np.ascontiguousarray(rgb, np.uint8))
+        masks.append(m)
+        outs.append(np.zeros((m.shape[0], m.shape[1], 3), np.uint8))
+    n = len(cases)
+    ptrs = lambda arrs: (ctypes.c_void_p * n)(*[a.ctypes.data for a in arrs])  # noqa: E731
+    ints = lambda vals: (ctypes.c_int * n)(*vals)  # noqa: E731
+    st = (ctypes.c_int * n)()
+    _check(lib.inpaint_batch_run(n, ptrs(rgbs), ptrs(masks), ints([m.shape[1] for m in masks]),
+                                 ints([m.shape[0] for m in masks]), ints([int(c[2]) for c in cases]),
+                                 ctypes.byref(opt), ptrs(outs), st), "inpaint_batch_run")
+    return outs, list(st)
 
 
 class Server:

@@ -1289,7 +1289,7 @@ int inpaint_batch_reset(inpaint_batch* b) {
   return INPAINT_OK;
 }
 
-int inpaint_batch_run(inpaint_batch* b, int max_iters, int* status_out) {
+int inpaint_batch_run_ctx(inpaint_batch* b, int max_iters, int* status_out) {
   if (!b) return INPAINT_ERR_ARG;
   int rc = INPAINT_OK;
   if (max_iters <= 0 && b->run_exec) {
@@ -1346,6 +1346,30 @@ void inpaint_batch_destroy(inpaint_batch* b) {
   if (!b) return;
   b->release();
   delete b;
+}
+
+int inpaint_batch_run(int n, const uint8_t* const* rgb, const uint8_t* const* mask, const int* w,
+                      const int* h, const int* r, const inpaint_options* opt, uint8_t* const* rgb_out,
+                      int* status_out) {
+  if (n <= 0 || !rgb || !mask || !w || !h || !r || !rgb_out) {
+    g_last_error = "inpaint_batch_run: n must be positive and every array non-null";
+    return INPAINT_ERR_ARG;
+  }
+  std::vector<inpaint_image> ims((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    if (!rgb[i] || !mask[i] || !rgb_out[i]) {
+      g_last_error = "inpaint_batch_run: null image pointer at index " + std::to_string(i);
+      return INPAINT_ERR_ARG;
+    }
+    ims[i] = inpaint_image{rgb[i], w[i], h[i], 3 * w[i], mask[i], w[i], r[i]};
+  }
+  inpaint_batch* b = nullptr;
+  int rc = inpaint_batch_create(ims.data(), n, opt, &b);
+  if (rc < 0) return rc;
+  rc = inpaint_batch_run_ctx(b, 0, status_out);
+  for (int i = 0; rc >= 0 && i < n; ++i) rc = inpaint_batch_result(b, i, rgb_out[i], 3 * w[i], nullptr, nullptr);
+  inpaint_batch_destroy(b);
+  return rc < 0 ? rc : INPAINT_OK;
 }
 
 }  // extern "C"

@@ -82,3 +82,18 @@ def test_bad_arguments_rejected_before_any_device_work():
     key = ctypes.c_uint64(5)
     assert lib.inpaint_search_rows(None, 0, 10, ctypes.byref(key)) == -1
     assert lib.inpaint_apply_key(None, 0, None) == -1
+
+
+def test_one_shot_batch_rejects_bad_arguments_before_any_device_work():
+    lib = _lib.load()
+    n = 2
+    buf = (ctypes.c_uint8 * (3 * 30 * 30))()
+    ptrs = (ctypes.c_void_p * n)(ctypes.addressof(buf), ctypes.addressof(buf))
+    nulls = (ctypes.c_void_p * n)(ctypes.addressof(buf), None)
+    ints = (ctypes.c_int * n)(30, 30)
+    radii = (ctypes.c_int * n)(2, 2)
+    st = (ctypes.c_int * n)()
+    assert lib.inpaint_batch_run(0, ptrs, ptrs, ints, ints, radii, None, ptrs, st) == -1
+    assert lib.inpaint_batch_run(n, None, ptrs, ints, ints, radii, None, ptrs, st) == -1
+    assert lib.inpaint_batch_run(n, ptrs, ptrs, ints, ints, radii, None, nulls, st) == -1
+    assert b"index 1" in lib.inpaint_last_error()

@@ -167,3 +167,17 @@ def test_batch_image_without_source_fails_alone(api):
         for i in solo:
             assert st[i] == 0, i
             assert np.array_equal(b.result(i)[0], solo[i]), i
+
+
+def test_one_shot_batch_run_equals_oracle(api):
+    # the one-shot C entry point (create, run, results, destroy in one call)
+    cases = mixed_cases(6, 41)
+    outs, st = api.batch_run(cases)
+    assert st == [0] * len(cases)
+    for i, (rgb, mask, r) in enumerate(cases):
+        assert np.array_equal(outs[i], oracle.run(rgb, mask, r).rgb), i
+    # an image without a source fails alone inside the one-shot call
+    bad = lattice_case()
+    outs, st = api.batch_run(cases[:2] + [bad])
+    assert st[:2] == [0, 0] and st[2] == -4
+    assert np.array_equal(outs[1], oracle.run(*cases[1]).rgb)
