@@ -60,12 +60,12 @@ int make_image_tmap_box(const ImgState& s, int box_w, int box_h, CUtensorMap* ou
   return encode_2d(s.img, s.W, s.H, s.pitch, box_w, box_h, out);
 }
 
-// The engine's two maps per image: out[0] the search window of RGBA words,
-// (128 + 2r rounded up to 4) x (16 * srw + 2r); out[1] the validity counts
-// of the batch's candidates, kEngCountW x (16 * srw) from a 4-word boundary.
+// The engine's two maps per image: out[0] the search window of RGBA words of
+// a batch, eng_tile_width(r, srw) x (32 + 2r); out[1] the validity counts of
+// the batch's candidates, eng_count_width(srw) x 32 from a 4-word boundary.
 int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out) {
-  if (make_image_tmap_box(s, (128 + 2 * s.r + 3) & ~3, kEngWarps * srw + 2 * s.r, out) != 0) return -1;
-  return encode_2d(s.count, s.W, s.H, s.pitch, kEngCountW, kEngWarps * srw, out + 1);
+  if (make_image_tmap_box(s, eng_tile_width(s.r, srw), kEngBatchRows + 2 * s.r, out) != 0) return -1;
+  return encode_2d(s.count, s.W, s.H, s.pitch, eng_count_width(srw), kEngBatchRows, out + 1);
 }
 
 }  // namespace inp

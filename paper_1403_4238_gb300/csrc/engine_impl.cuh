@@ -25,209 +25,241 @@ namespace inp {
 
 // ---------------------------------------------------------------- search batch
 
+// A search batch is 32 candidate rows x BWC candidate columns.  Lane l of
+// warp w owns the NCL adjacent candidates (row l, columns w*NCL ...): every
+// lane of a warp uses the same target row at the same time (the row-mask
+// branch stays warp-uniform), and the lanes' 128-bit loads of their source
+// row strips fall on 32 consecutive tile rows, conflict-free.
 template <int R, int SRW>
 struct EngGeom {
   static constexpr int P = 2 * R + 1;
-  static constexpr int BW = (128 + 2 * R + 3) & ~3;  // staged width (words)
-  static constexpr int B = kEngWarps * SRW;          // candidate rows per batch
-  static constexpr int BH = B + 2 * R;               // staged rows
+  static constexpr int NCL = 4 * SRW;              // candidates per lane (4 or 8)
+  static constexpr int BWC = eng_batch_cols(SRW);  // candidate columns per batch (64 or 128)
+  static constexpr int B = kEngBatchRows;          // candidate rows per batch (one per lane)
+  static constexpr int BW = eng_tile_width(R, SRW);  // staged width (words)
+  static constexpr int BH = B + 2 * R;             // staged rows
   static constexpr int PIX_BYTES = ((BW * BH * 4 + 127) / 128) * 128;
-  static constexpr int CNT_BYTES = ((kEngCountW * B * 4 + 127) / 128) * 128;
-  static constexpr int STAGE_BYTES = PIX_BYTES + CNT_BYTES;  // pixel tile | count tile
+  static constexpr int CW = eng_count_width(SRW);  // count tile width (words), CW / 4 odd
+  static constexpr int CNT_BYTES = ((CW * B * 4 + 127) / 128) * 128;
+  static constexpr int VB_BYTES = kEngWarps * 32;  // validity bits: one byte per (warp, lane)
+  static constexpr int SLOT_BYTES = PIX_BYTES + VB_BYTES;
   static constexpr int COFF = R & 3;  // first candidate column within the count tile
-  static constexpr int NROW = (4 + P - 1 + 3) & ~3;  // strip words per lane
+  static constexpr int NS = (NCL + P - 1 + 3) & ~3;  // strip words per lane
   static constexpr int TP = (P + 3) & ~3;            // padded target row (words)
   static constexpr unsigned FULL = (1u << P) - 1u;
+  static_assert((kEngWarps - 1) * NCL + NS <= BW, "row strip must stay inside the tile");
+  static_assert(kEngWarps * NCL + 4 <= CW, "count chunk must stay inside the tile row");
+  static_assert(((CW / 4) & 1) == 1, "count rows must start in different bank quadruples");
 };
 
-// SSD of the SRW x 4 candidates of this lane (rows row0.. of the batch,
-// columns lane*4..lane*4+3) against the staged target.  Fully-known target
-// rows take a branch-free path; partly-known rows test a bit mask per column
-// (warp-uniform).
-template <int R, int SRW>
-__device__ inline void compute_rows(const uint32_t* __restrict__ stage, int row0,
-                                    const uint32_t* __restrict__ tgt,
-                                    const uint32_t* __restrict__ rowmask, uint32_t (&acc)[SRW][4]) {
-  using G = EngGeom<R, SRW>;
-  constexpr int P = G::P, BW = G::BW, NROW = G::NROW;
-  const int lane = threadIdx.x & 31;
+template <int N>
+__device__ __forceinline__ void lds_words(uint32_t (&d)[N], const uint32_t* p) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
 #pragma unroll
-  for (int o = 0; o < SRW; ++o)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[o][k] = 0;
-#pragma unroll
-  for (int sr = 0; sr < SRW + 2 * R; ++sr) {
-    uint32_t row[NROW];
-    const uint4* sp = reinterpret_cast<const uint4*>(stage + (row0 + sr) * BW + lane * 4);
-#pragma unroll
-    for (int i = 0; i < NROW / 4; ++i) {
-      const uint4 v = sp[i];
-      row[4 * i] = v.x;
-      row[4 * i + 1] = v.y;
-      row[4 * i + 2] = v.z;
-      row[4 * i + 3] = v.w;
-    }
-#pragma unroll
-    for (int o = 0; o < SRW; ++o) {
-      const int dy = sr - o;
-      if (dy < 0 || dy >= P) continue;
-      const uint32_t m = rowmask[dy];
-      if (m == 0) continue;
-      uint32_t t[G::TP];
-      const uint4* tp = reinterpret_cast<const uint4*>(tgt + dy * G::TP);
-#pragma unroll
-      for (int i = 0; i < G::TP / 4; ++i) {
-        const uint4 v = tp[i];
-        t[4 * i] = v.x;
-        t[4 * i + 1] = v.y;
-        t[4 * i + 2] = v.z;
-        t[4 * i + 3] = v.w;
-      }
-      if (m == G::FULL) {
-#pragma unroll
-        for (int dx = 0; dx < P; ++dx) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint32_t d = __vabsdiffu4(t[dx], row[k + dx]);
-            acc[o][k] = __dp4a(d, d, acc[o][k]);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int dx = 0; dx < P; ++dx) {
-          if (m & (1u << dx)) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const uint32_t d = __vabsdiffu4(t[dx], row[k + dx]);
-              acc[o][k] = __dp4a(d, d, acc[o][k]);
-            }
-          }
-        }
-      }
-    }
+  for (int i = 0; i < N / 4; ++i) {
+    const uint4 v = q[i];
+    d[4 * i] = v.x;
+    d[4 * i + 1] = v.y;
+    d[4 * i + 2] = v.z;
+    d[4 * i + 3] = v.w;
   }
 }
 
-// Two-row batches (SRW = 2): half-warps take two adjacent candidate rows and
-// each lane eight adjacent candidates (columns (lane & 15) * 8 ...), so both
-// half-warps use the same target row at a time: the row-mask branch stays
-// warp-uniform and costs half as much per evaluation as with four candidates.
-// SSD terms of target columns dx in [D0, D0 + L) for eight candidates, no
-// per-column test (a contiguous run of known target pixels).
-template <int R, int D0, int L, int TP, int N8>
-__device__ __forceinline__ void ssd_run8(const uint32_t (&t)[TP], const uint32_t (&r)[N8],
-                                         uint32_t (&acc)[16]) {
-  // even and odd columns go to separate accumulators: twice the independent
-  // dot-product chains per lane
-#pragma unroll
-  for (int dx = D0; dx < D0 + L; ++dx)
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
-      acc[(dx & 1) * 8 + k] = __dp4a(d, d, acc[(dx & 1) * 8 + k]);
-    }
+// Row descriptor of a target row (computed once per target): which of its
+// P pixels are known.  A row next to the fill front is usually known on one
+// contiguous run that touches one end of the row, so the common shapes take
+// one jump into a straight run of code instead of a test per column:
+//   kRowSkip   nothing known;
+//   kRowFrom   known on [s, P) (s = 0: the whole row), s in the low bits;
+//   kRowUpTo   known on [0, e), e in the low bits;
+//   kRowMask   anything else, the bit mask of known columns in the low bits.
+constexpr uint32_t kRowSkip = 0u, kRowFrom = 1u << 30, kRowUpTo = 2u << 30, kRowMask = 3u << 30;
+
+__device__ __forceinline__ uint32_t row_desc(uint32_t m, int P) {
+  const uint32_t full = (1u << P) - 1u;
+  if (m == 0) return kRowSkip;
+  const int s = __ffs(m) - 1;           // lowest known column
+  const int e = 32 - __clz(m);          // one past the highest known column
+  if (m == ((full >> s) << s)) return kRowFrom | (uint32_t)s;
+  if (s == 0 && m == (1u << e) - 1u) return kRowUpTo | (uint32_t)e;
+  return kRowMask | m;
 }
 
-template <int R>
-__device__ inline void compute_rows8(const uint32_t* __restrict__ stage, int row, int col,
-                                     const uint32_t* __restrict__ tgt,
-                                     const uint32_t* __restrict__ rowmask, uint32_t (&acc)[8]) {
-  using G = EngGeom<R, 2>;
-  constexpr int P = G::P, BW = G::BW, N8 = (8 + P - 1 + 3) & ~3;
-  static_assert(15 * 8 + N8 <= BW, "row strip must stay inside the tile");
-  uint32_t acc2[16];
+// SSD terms of target column DX for the lane's NCL candidates.
+#define INP_SSD_COL(DX)                                                   \
+  if constexpr ((DX) < P) {                                               \
+    _Pragma("unroll") for (int k = 0; k < NCL; ++k) {                     \
+      const uint32_t d_ = __vabsdiffu4(t[(DX)], r[k + (DX)]);             \
+      acc[k] = __dp4a(d_, d_, acc[k]);                                    \
+    }                                                                     \
+  }
+
+// SSD of this lane's NCL candidates against the staged target (Eq. 4): for
+// every known target pixel one byte-SIMD absolute difference and one 4-way
+// byte dot product per candidate (|a-b| per channel, squares summed; alpha
+// is 0 on both sides).  `strip` points at the lane's row strip in the tile
+// (row = lane, column = warp * NCL); `rowd` holds one row descriptor per
+// target row.  A run of known columns [s, P) enters an ascending sequence of
+// columns at s, a run [0, e) a descending one at e - 1 (one warp-uniform
+// indirect jump per row); other rows test a bit per column.
+template <int R, int SRW>
+__device__ __forceinline__ void unit_ssd(const uint32_t* __restrict__ strip,
+                                         const uint32_t* __restrict__ tgt,
+                                         const uint32_t* __restrict__ rowd,
+                                         uint32_t (&acc)[4 * SRW]) {
+  using G = EngGeom<R, SRW>;
+  constexpr int P = G::P, NS = G::NS, NCL = G::NCL, BW = G::BW, TP = G::TP;
+  static_assert(P <= 17, "column sequences are written out for P <= 17");
 #pragma unroll
-  for (int k = 0; k < 16; ++k) acc2[k] = 0;
+  for (int k = 0; k < NCL; ++k) acc[k] = 0;
 #pragma unroll 1
   for (int dy = 0; dy < P; ++dy) {
-    const uint32_t m = rowmask[dy];
-    if (m == 0) continue;
-    uint32_t r[N8];
-    const uint4* sp = reinterpret_cast<const uint4*>(stage + (row + dy) * BW + col);
-#pragma unroll
-    for (int i = 0; i < N8 / 4; ++i) {
-      const uint4 v = sp[i];
-      r[4 * i] = v.x;
-      r[4 * i + 1] = v.y;
-      r[4 * i + 2] = v.z;
-      r[4 * i + 3] = v.w;
-    }
-    uint32_t t[G::TP];
-    const uint4* tp = reinterpret_cast<const uint4*>(tgt + dy * G::TP);
-#pragma unroll
-    for (int i = 0; i < G::TP / 4; ++i) {
-      const uint4 v = tp[i];
-      t[4 * i] = v.x;
-      t[4 * i + 1] = v.y;
-      t[4 * i + 2] = v.z;
-      t[4 * i + 3] = v.w;
-    }
-    const uint32_t um = ~m & G::FULL;  // unknown columns of the row
-    if (m == G::FULL) {
-      ssd_run8<R, 0, P>(t, r, acc2);
-    } else if ((m & (m + 1)) == 0 || (um & (um + 1)) == 0) {
-      // the known columns are one run at the start or at the end of the row
-      // (the usual shape next to the fill front): straight-line code
-      const bool at_end = (m & 1u) == 0;
-      switch (__popc(m)) {
-#define INP_RUN8(n)                                             \
-  case n:                                                       \
-    if constexpr (n < P) {                                      \
-      if (at_end) ssd_run8<R, P - n, n>(t, r, acc2);            \
-      else ssd_run8<R, 0, n>(t, r, acc2);                       \
-    }                                                           \
-    break;
-        INP_RUN8(1) INP_RUN8(2) INP_RUN8(3) INP_RUN8(4) INP_RUN8(5) INP_RUN8(6) INP_RUN8(7)
-        INP_RUN8(8) INP_RUN8(9) INP_RUN8(10) INP_RUN8(11) INP_RUN8(12) INP_RUN8(13) INP_RUN8(14)
-        INP_RUN8(15) INP_RUN8(16)
-#undef INP_RUN8
-        default:
-          break;
+    const uint32_t desc = rowd[dy];
+    if (desc == kRowSkip) continue;
+    uint32_t r[NS], t[TP];
+    lds_words(r, strip + dy * BW);
+    lds_words(t, tgt + dy * TP);
+    const uint32_t kind = desc & (3u << 30), arg = desc & 0xffffu;
+    if (kind == kRowFrom) {
+      switch (arg) {
+        case 0: INP_SSD_COL(0) [[fallthrough]];
+        case 1: INP_SSD_COL(1) [[fallthrough]];
+        case 2: INP_SSD_COL(2) [[fallthrough]];
+        case 3: INP_SSD_COL(3) [[fallthrough]];
+        case 4: INP_SSD_COL(4) [[fallthrough]];
+        case 5: INP_SSD_COL(5) [[fallthrough]];
+        case 6: INP_SSD_COL(6) [[fallthrough]];
+        case 7: INP_SSD_COL(7) [[fallthrough]];
+        case 8: INP_SSD_COL(8) [[fallthrough]];
+        case 9: INP_SSD_COL(9) [[fallthrough]];
+        case 10: INP_SSD_COL(10) [[fallthrough]];
+        case 11: INP_SSD_COL(11) [[fallthrough]];
+        case 12: INP_SSD_COL(12) [[fallthrough]];
+        case 13: INP_SSD_COL(13) [[fallthrough]];
+        case 14: INP_SSD_COL(14) [[fallthrough]];
+        case 15: INP_SSD_COL(15) [[fallthrough]];
+        case 16: INP_SSD_COL(16) [[fallthrough]];
+        default: break;
+      }
+    } else if (kind == kRowUpTo) {
+      switch (arg) {
+        case 17: INP_SSD_COL(16) [[fallthrough]];
+        case 16: INP_SSD_COL(15) [[fallthrough]];
+        case 15: INP_SSD_COL(14) [[fallthrough]];
+        case 14: INP_SSD_COL(13) [[fallthrough]];
+        case 13: INP_SSD_COL(12) [[fallthrough]];
+        case 12: INP_SSD_COL(11) [[fallthrough]];
+        case 11: INP_SSD_COL(10) [[fallthrough]];
+        case 10: INP_SSD_COL(9) [[fallthrough]];
+        case 9: INP_SSD_COL(8) [[fallthrough]];
+        case 8: INP_SSD_COL(7) [[fallthrough]];
+        case 7: INP_SSD_COL(6) [[fallthrough]];
+        case 6: INP_SSD_COL(5) [[fallthrough]];
+        case 5: INP_SSD_COL(4) [[fallthrough]];
+        case 4: INP_SSD_COL(3) [[fallthrough]];
+        case 3: INP_SSD_COL(2) [[fallthrough]];
+        case 2: INP_SSD_COL(1) [[fallthrough]];
+        case 1: INP_SSD_COL(0) [[fallthrough]];
+        default: break;
       }
     } else {
+      const uint32_t m = desc;  // kRowMask: bits of the known columns (P <= 17 < 30)
 #pragma unroll
       for (int dx = 0; dx < P; ++dx) {
         if (m & (1u << dx)) {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < NCL; ++k) {
             const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
-            acc2[(dx & 1) * 8 + k] = __dp4a(d, d, acc2[(dx & 1) * 8 + k]);
+            acc[k] = __dp4a(d, d, acc[k]);
           }
         }
       }
     }
   }
+}
+#undef INP_SSD_COL
+
+// The compute of a search round, outside the engine body so that its
+// registers hold only the row strips, the target row and the accumulators
+// (the engine body keeps the leader's state live across the search).
+
+// Smallest key (SSD << 32 | idx) of this lane's candidates in one unit:
+// `bits` marks the valid ones, idx0 is the linear index of the first.
+template <int R, int SRW>
+__device__ __noinline__ unsigned long long unit_best(const uint32_t* strip, const uint32_t* tgt,
+                                                     const uint32_t* rowd, uint32_t bits, unsigned idx0) {
+  uint32_t acc[4 * SRW];
+  unit_ssd<R, SRW>(strip, tgt, rowd, acc);
+  unsigned long long best = ~0ull;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) acc[k] = acc2[k] + acc2[8 + k];
+  for (int k = 0; k < 4 * SRW; ++k) {
+    const unsigned long long key = ((unsigned long long)acc[k] << 32) | (idx0 + (unsigned)k);
+    if ((bits & (1u << k)) && key < best) best = key;
+  }
+  return best;
+}
+
+// All units of a CTA whose batches are resident: slot i holds batch
+// rank + i * ns of the image (tile, then the validity bits per (warp, lane)).
+template <int R, int SRW>
+__device__ __noinline__ unsigned long long resident_units(const uint8_t* slots, int nmine, int rank, int ns,
+                                                          int ncg, int xb, int cy0, int W,
+                                                          const uint32_t* tgt, const uint32_t* rowd) {
+  using G = EngGeom<R, SRW>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long best = ~0ull;
+#pragma unroll 1
+  for (int i = 0; i < nmine; ++i) {
+    const int b = rank + i * ns, gx = b % ncg, gy = b / ncg;
+    const uint8_t* slot = slots + (size_t)i * G::SLOT_BYTES;
+    const uint32_t bits = slot[G::PIX_BYTES + warp * 32 + lane];
+    const unsigned idx0 = (unsigned)((cy0 + G::B * gy + lane) * W + xb + G::BWC * gx + G::NCL * warp);
+    uint32_t acc[G::NCL];
+    unit_ssd<R, SRW>(reinterpret_cast<const uint32_t*>(slot) + lane * G::BW + G::NCL * warp, tgt, rowd, acc);
+#pragma unroll
+    for (int k = 0; k < G::NCL; ++k) {
+      const unsigned long long key = ((unsigned long long)acc[k] << 32) | (idx0 + (unsigned)k);
+      if ((bits & (1u << k)) && key < best) best = key;
+    }
+  }
+  return best;
 }
 
 // ---------------------------------------------------------------- kernel
 
 struct EngSmemTail {
-  uint64_t full[2];  // TMA completion barriers of the two stages
+  uint64_t full[2];  // TMA completion barriers of the two streaming stages
   ImgState img;      // the image's state block (a leader that does not search reads it here)
   unsigned long long red64[32];
   int red32[32];
   int flag;
   int stop;
   int px, py;
-  uint8_t known[17 * 17];
+  uint8_t known[2][17 * 17];  // known flags of the last two targets (by round parity)
 };
 
 constexpr int kTgtWords = 17 * 20 + 17 + 3;  // padded target rows + row masks (R <= 8)
 constexpr size_t kHeadBytes = ((((sizeof(EngSmemTail) + 15) & ~size_t(15)) + kTgtWords * 4 + 127) / 128) * 128;
 
-// Shared memory of an engine CTA: head | two search stages | update state |
-// update cache (the leader keeps its speculative state while it searches).
+// Shared memory of an engine CTA: head | (the leader only) update state and
+// update cache | two count tiles | tile slots.  The slots hold the source
+// tiles of the CTA's search batches: all of them, resident across the
+// iterations of a removal, when they fit, else two used as a double buffer.
+// A searching CTA that does not lead starts its count tiles right after the
+// head.  The kernel is launched with all the shared memory an SM offers and
+// takes as many slots as fit.
 template <int R>
 __host__ __device__ constexpr size_t upd_smem_bytes() {
   return ((sizeof(UpdSmem<R>) + 127) / 128) * 128 + sizeof(UpdCache<R>);
 }
 
+// The least shared memory an engine CTA needs: a searching leader with two
+// slots (the streaming double buffer).
 template <int R, int SRW>
 __host__ __device__ constexpr size_t eng_smem_bytes() {
   using G = EngGeom<R, SRW>;
-  return kHeadBytes + (size_t)2 * G::STAGE_BYTES + upd_smem_bytes<R>() + 128;
+  return kHeadBytes + ((upd_smem_bytes<R>() + 127) / 128) * 128 + (size_t)2 * G::CNT_BYTES +
+         (size_t)2 * G::SLOT_BYTES + 128;
 }
 
 static_assert(eng_smem_bytes<8, 2>() <= 227 * 1024, "engine CTA must fit in shared memory");
@@ -330,12 +362,10 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   uint8_t* smem = x.smem;
   EngSmemTail& tl = *reinterpret_cast<EngSmemTail*>(smem);
   uint32_t* tgt = reinterpret_cast<uint32_t*>(smem + ((sizeof(EngSmemTail) + 15) & ~size_t(15)));
-  uint32_t* rowmask = tgt + P * G::TP;
-  uint8_t* big = smem + kHeadBytes;
-  uint32_t* stage0 = reinterpret_cast<uint32_t*>(big);
-  uint32_t* stage1 = reinterpret_cast<uint32_t*>(big + G::STAGE_BYTES);
-  UpdSmem<R>& usm = *reinterpret_cast<UpdSmem<R>*>(big + 2 * G::STAGE_BYTES);
-  UpdCache<R>& uca = upd_cache_of<R>(big + 2 * G::STAGE_BYTES);
+  uint32_t* rowd = tgt + P * G::TP;  // row descriptors of the target
+  uint8_t* upd_base = smem + kHeadBytes;
+  UpdSmem<R>& usm = *reinterpret_cast<UpdSmem<R>*>(upd_base);
+  UpdCache<R>& uca = upd_cache_of<R>(upd_base);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rank = x.rank, tsize = x.tsize;
   TeamCtl* tc = x.tc;
@@ -344,18 +374,18 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   uint32_t ph0 = x.ph0, ph1 = x.ph1;
   unsigned epoch = x.epoch;
 
-  // a leader that does not search reads the image's fields from shared
-  // memory, which keeps about forty registers free for its phases
-  if constexpr (kLeadOnly) {
+  // every role reads the image's fields from shared memory, which keeps
+  // about forty registers free for its phases
+  if constexpr (!kLeadOnly) {
     if (tid == 0) tl.img = ea.imgs[j];
     __syncthreads();
   }
-  std::conditional_t<kLeadOnly, const ImgState&, const ImgState> s = kLeadOnly ? tl.img : ea.imgs[j];
+  const ImgState& s = tl.img;
   const CUtensorMap* map = &ea.tmaps[2 * j];
   const CUtensorMap* cmap = &ea.tmaps[2 * j + 1];
   Ctrl* c = s.ctrl;
   const int xb = R + ((s.cx0 - R) & ~3);
-  const int ncg = s.cx1 >= s.cx0 ? (s.cx1 - xb + 128) / 128 : 0;
+  const int ncg = s.cx1 >= s.cx0 ? (s.cx1 - xb + G::BWC) / G::BWC : 0;
   const int nrb = s.cy1 >= s.cy0 ? (s.cy1 - s.cy0 + B) / B : 0;
   const int nbatch = ncg * nrb;
   // Roles: CTAs [0, ns) search, batch b going to CTA b mod ns (batches cost
@@ -377,7 +407,19 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       return;
     }
   }
-  bool resident = false;  // stage0 holds this CTA's only batch of the image
+  // count tiles and slots (a searching leader keeps its update state below them)
+  uint8_t* area = smem + kHeadBytes + (leader ? ((upd_smem_bytes<R>() + 127) / 128) * 128 : 0);
+  uint32_t* cnt_t[2] = {reinterpret_cast<uint32_t*>(area),
+                        reinterpret_cast<uint32_t*>(area + G::CNT_BYTES)};
+  uint8_t* slots = area + 2 * G::CNT_BYTES;
+  const int nslots = (int)((x.smem_end - slots) / G::SLOT_BYTES);
+  const int nmine = rank < ns ? (nbatch - rank + ns - 1) / ns : 0;  // batches rank, rank + ns, ...
+  // every batch of this CTA keeps its tile in a slot of its own across the
+  // iterations; the filled pixels and the validity of the candidates near
+  // each target are refreshed after the publication instead of a reload
+  const bool resident = nmine >= 1 && nmine <= nslots;
+  auto slot_pix = [&](int i) { return reinterpret_cast<uint32_t*>(slots + (size_t)i * G::SLOT_BYTES); };
+  auto slot_vb = [&](int i) { return slots + (size_t)i * G::SLOT_BYTES + G::PIX_BYTES; };
   if (tid == 0) {
     tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
     tl.px = __ldcg(&c->px);
@@ -385,124 +427,149 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   }
   __syncthreads();
   int prev_px = -1000000, prev_py = -1000000;
+  int round = 0;        // search rounds of this image in this launch
   bool staged = false;  // leader: neighbourhood of the next p^ already in shared memory
 
   // One search round for target (px, py): this CTA's batches; returns its
   // best key.  Whole block.
   auto search_round = [&](int px, int py) -> unsigned long long {
     const int b0 = rank < ns ? rank : nbatch;
-    const bool need0 = !resident ||
-                       (abs(prev_px - (xb + 128 * (b0 % max(ncg, 1)) + 64)) <= 64 + 2 * R + 4 &&
-                        abs(prev_py - (s.cy0 + B * (b0 / max(ncg, 1)) + B / 2)) <= B / 2 + 2 * R + 1);
-    // a batch's stage: its RGBA window (unless still resident) and the
-    // validity counts of its candidates, on one mbarrier
-    auto issue = [&](int b, uint32_t* st, uint64_t* bar, bool pixels) {
+    const int par = round & 1;
+    // a batch's stage in streaming mode: its RGBA window and the validity
+    // counts of its candidates, on one mbarrier
+    auto issue = [&](int b, uint32_t* st, uint32_t* ct, uint64_t* bar) {
       const int gx = b % ncg, gy = b / ncg;
       // (the stage's previous generic reads are ordered before this by the
       // block barrier that ends every batch)
-      mbar_expect_tx(bar, (uint32_t)((pixels ? G::BW * G::BH * 4 : 0) + kEngCountW * B * 4));
-      if (pixels) tma_load_2d(st, map, xb - R + 128 * gx, s.cy0 + B * gy - R, bar);
-      tma_load_2d(reinterpret_cast<uint8_t*>(st) + G::PIX_BYTES, cmap, xb - G::COFF + 128 * gx,
-                  s.cy0 + B * gy, bar);
+      mbar_expect_tx(bar, (uint32_t)(G::BW * G::BH * 4 + G::CW * B * 4));
+      tma_load_2d(st, map, xb - R + G::BWC * gx, s.cy0 + B * gy - R, bar);
+      tma_load_2d(ct, cmap, xb - G::COFF + G::BWC * gx, s.cy0 + B * gy, bar);
     };
-    if (tid == 0 && b0 < nbatch) issue(b0, stage0, &tl.full[0], need0);
-    // target patch: one thread per pixel, then the row masks
-    if (tid < P * P) {
-      const int tx = px + tid % P - R, ty = py + tid / P - R;
-      uint32_t w = 0;
-      int known = 0;
-      if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H) {
-        // both reads in flight together; the pixel is kept only if known
-        const uint8_t o = __ldcg(&s.omega[(size_t)ty * s.W + tx]);
-        const uint32_t v = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
-        known = o == 0;
-        w = known ? v : 0u;
+    const bool first = round == 0;
+    if (resident) {
+      if (first && tid == 0) {
+        // every tile of the CTA at once
+        mbar_expect_tx(&tl.full[0], (uint32_t)(nmine * G::BW * G::BH * 4));
+        for (int i = 0; i < nmine; ++i) {
+          const int b = rank + i * ns, gx = b % ncg, gy = b / ncg;
+          tma_load_2d(slot_pix(i), map, xb - R + G::BWC * gx, s.cy0 + B * gy - R, &tl.full[0]);
+        }
       }
-      tgt[(tid / P) * G::TP + tid % P] = w;
-      tl.known[tid] = (uint8_t)known;
+    } else if (tid == 0 && b0 < nbatch) {
+      issue(b0, slot_pix(0), cnt_t[0], &tl.full[0]);
     }
-    __syncthreads();
-    if (tid < P) {
-      uint32_t m = 0;
-      for (int dx = 0; dx < P; ++dx) m |= (uint32_t)tl.known[tid * P + dx] << dx;
-      rowmask[tid] = m;
+    if (resident && first) {
+      // validity bits of every candidate of the CTA's batches
+      for (int i = 0; i < nmine; ++i) {
+        const int b = rank + i * ns, gx = b % ncg, gy = b / ncg;
+        const int qy = s.cy0 + B * gy + lane, qx0 = xb + G::BWC * gx + G::NCL * warp;
+        uint32_t bits = 0;
+        if (qy <= s.cy1) {
+#pragma unroll
+          for (int k = 0; k < G::NCL; ++k) {
+            const int qx = qx0 + k;
+            if (qx >= s.cx0 && qx <= s.cx1 && __ldcg(&s.count[(size_t)qy * s.pitch + qx]) == 0)
+              bits |= 1u << k;
+          }
+        }
+        slot_vb(i)[warp * 32 + lane] = (uint8_t)bits;
+      }
+    } else if (resident) {
+      // the previous target's filled pixels (its unknown in-image pixels),
+      // copied by the leader before the publication, into every tile
+      // window that holds them
+      const uint8_t* kprev = tl.known[par ^ 1];
+      if (tid < P * P) {
+        const int tx = prev_px + tid % P - R, ty = prev_py + tid / P - R;
+        if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H && !kprev[tid]) {
+          const uint32_t w = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
+          for (int i = 0; i < nmine; ++i) {
+            const int b = rank + i * ns, gx = b % ncg, gy = b / ncg;
+            const int lx = tx - (xb - R + G::BWC * gx), ly = ty - (s.cy0 + B * gy - R);
+            if (lx >= 0 && lx < G::BW && ly >= 0 && ly < G::BH) slot_pix(i)[ly * G::BW + lx] = w;
+          }
+        }
+      }
+      // candidates within 2R of the previous target may have become valid
+      constexpr int NCW = 4 * R + 1;
+      for (int jj = tid; jj < NCW * NCW; jj += kEngThreads) {
+        const int qx = prev_px + jj % NCW - 2 * R, qy = prev_py + jj / NCW - 2 * R;
+        if (qx < s.cx0 || qx > s.cx1 || qy < s.cy0 || qy > s.cy1) continue;
+        const int gx = (qx - xb) / G::BWC, gy = (qy - s.cy0) / B, b = gy * ncg + gx;
+        if (b % ns != rank) continue;
+        if (__ldcg(&s.count[(size_t)qy * s.pitch + qx]) != 0) continue;
+        const int cx = (qx - xb) % G::BWC, e = (cx / G::NCL) * 32 + (qy - s.cy0) % B;
+        uint8_t* vb = slot_vb((b - rank) / ns);
+        atomicOr(reinterpret_cast<unsigned*>(vb + (e & ~3)), (1u << (cx % G::NCL)) << (8 * (e & 3)));
+      }
+    }
+    // target patch: warp dy reads row dy (lane = dx); the ballot of the
+    // known flags gives the row descriptor
+    {
+      uint8_t* kn = tl.known[par];
+      for (int dy = warp; dy < P; dy += kEngWarps) {
+        const int tx = px + lane - R, ty = py + dy - R;
+        uint32_t w = 0;
+        bool known = false;
+        if (lane < P && tx >= 0 && tx < s.W && ty >= 0 && ty < s.H) {
+          // both reads in flight together; the pixel is kept only if known
+          const uint8_t o = __ldcg(&s.omega[(size_t)ty * s.W + tx]);
+          const uint32_t v = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
+          known = o == 0;
+          w = known ? v : 0u;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, known);
+        if (lane < P) {
+          tgt[dy * G::TP + lane] = w;
+          kn[dy * P + lane] = (uint8_t)known;
+        }
+        if (lane == 0) rowd[dy] = row_desc(bal & G::FULL, P);
+      }
     }
     __syncthreads();
     unsigned long long best = ~0ull;
-    int cur = 0;
     bool ok = true;
-    int nproc = 0;
-    for (int b = b0; b < nbatch; b += ns) {
-      const int nb = b + ns;
-      if (tid == 0 && nb < nbatch) issue(nb, cur ? stage0 : stage1, &tl.full[cur ^ 1], true);
-      const int gx = b % ncg, gy = b / ncg;
-      const int qx0 = xb + 128 * gx + lane * 4, qy0 = s.cy0 + B * gy + warp * SRW;
-      const bool got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
-      if (cur) ph1 ^= 1; else ph0 ^= 1;
-      const uint32_t* stg = cur ? stage1 : stage0;
-      const int* cst = reinterpret_cast<const int*>(reinterpret_cast<const uint8_t*>(stg) + G::PIX_BYTES);
-      if constexpr (SRW == 2) {
-        // lane: candidate row warp*2 + lane/16, columns (lane & 15)*8 + [0, 8)
-        const int lrow = warp * 2 + (lane >> 4), lcol = (lane & 15) * 8;
-        uint32_t acc[8];
-        compute_rows8<R>(stg, lrow, lcol, tgt, rowmask, acc);
-        const int qy = s.cy0 + B * gy + lrow;
-        int cw[12];  // counts of this lane's candidates (vector loads, 16-byte aligned)
-        const int4* cp4 = reinterpret_cast<const int4*>(cst + lrow * kEngCountW + lcol);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const int4 v = cp4[i];
-          cw[4 * i] = v.x;
-          cw[4 * i + 1] = v.y;
-          cw[4 * i + 2] = v.z;
-          cw[4 * i + 3] = v.w;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int qx = xb + 128 * gx + lcol + k;
-          const bool in = qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1;
-          if (in && cw[G::COFF + k] == 0) {
-            const unsigned idx = (unsigned)(qy * s.W + qx);
-            const unsigned long long key = ((unsigned long long)acc[k] << 32) | idx;
-            best = key < best ? key : best;
-          }
-        }
-      } else {
-        uint32_t acc[SRW][4];
-        compute_rows<R, SRW>(stg, warp * SRW, tgt, rowmask, acc);
-#pragma unroll
-        for (int o = 0; o < SRW; ++o) {
-          int cw[8];  // counts of this lane's candidates (vector loads, 16-byte aligned)
-          const int4* cp4 = reinterpret_cast<const int4*>(cst + (warp * SRW + o) * kEngCountW + lane * 4);
-          const int4 v0 = cp4[0], v1 = cp4[1];
-          cw[0] = v0.x; cw[1] = v0.y; cw[2] = v0.z; cw[3] = v0.w;
-          cw[4] = v1.x; cw[5] = v1.y; cw[6] = v1.z; cw[7] = v1.w;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int qx = qx0 + k, qy = qy0 + o;
-            const bool in = qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1;
-            if (in && cw[G::COFF + k] == 0) {
-              const unsigned idx = (unsigned)(qy * s.W + qx);
-              const unsigned long long key = ((unsigned long long)acc[o][k] << 32) | idx;
-              best = key < best ? key : best;
-            }
-          }
-        }
+    if (resident) {
+      if (first) {
+        ok = mbar_wait(&tl.full[0], ph0, limit);
+        ph0 ^= 1;
       }
-      ++nproc;
-      if (__syncthreads_or(!got)) {  // a bounded wait gave up: stop uniformly
-        ok = false;
-        if (nb < nbatch) {
-          mbar_wait(&tl.full[cur ^ 1], cur ? ph0 : ph1, limit);
-          if (cur) ph0 ^= 1; else ph1 ^= 1;
+      if (ok) best = resident_units<R, SRW>(slots, nmine, rank, ns, ncg, xb, s.cy0, s.W, tgt, rowd);
+      ok = !__syncthreads_or(!ok);
+    } else {
+      int cur = 0;
+      for (int b = b0; b < nbatch; b += ns) {
+        const int nb = b + ns;
+        if (tid == 0 && nb < nbatch) issue(nb, slot_pix(cur ^ 1), cnt_t[cur ^ 1], &tl.full[cur ^ 1]);
+        const int gx = b % ncg, gy = b / ncg;
+        const bool got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
+        if (cur) ph1 ^= 1; else ph0 ^= 1;
+        // validity of this lane's candidates from the count tile (16-byte
+        // aligned chunk) and the search rectangle
+        uint32_t cw[G::NCL + 4];
+        lds_words(cw, cnt_t[cur] + lane * G::CW + G::NCL * warp);
+        const int qy = s.cy0 + B * gy + lane, qx0 = xb + G::BWC * gx + G::NCL * warp;
+        uint32_t bits = 0;
+#pragma unroll
+        for (int k = 0; k < G::NCL; ++k) {
+          const int qx = qx0 + k;
+          if (qx >= s.cx0 && qx <= s.cx1 && qy <= s.cy1 && cw[G::COFF + k] == 0) bits |= 1u << k;
         }
-        break;
+        const unsigned long long kb = unit_best<R, SRW>(slot_pix(cur) + lane * G::BW + G::NCL * warp, tgt, rowd,
+                                                        bits, (unsigned)(qy * s.W + qx0));
+        best = kb < best ? kb : best;
+        if (__syncthreads_or(!got)) {  // a bounded wait gave up: stop uniformly
+          ok = false;
+          if (nb < nbatch) {
+            mbar_wait(&tl.full[cur ^ 1], cur ? ph0 : ph1, limit);
+            if (cur) ph0 ^= 1; else ph1 ^= 1;
+          }
+          break;
+        }
+        cur ^= 1;
       }
-      cur ^= 1;
     }
-    // the tile stays resident when it was this CTA's only batch (the leader's
-    // shared memory is reused by its update phase)
-    resident = ok && !leader && b0 < nbatch && nproc == 1;
+    ++round;
     if (!ok && tid == 0) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
     return block_min_u64(best, tl.red64);
   };

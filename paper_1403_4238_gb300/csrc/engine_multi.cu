@@ -33,6 +33,9 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   EngCtx x;
   x.smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint32_t dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  x.smem_end = smem_raw + dyn;
   const int team = ea.cta_team[blockIdx.x];
   const int first = ea.team_first[team];
   x.rank = blockIdx.x - first;
@@ -65,6 +68,19 @@ cudaError_t engine_occupancy(size_t smem, int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine, kEngThreads, smem);
+}
+
+size_t engine_launch_smem() {
+  static size_t cached = 0;
+  if (cached) return cached;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_engine) != cudaSuccess)
+    return 0;
+  cached = (size_t)optin - fa.sharedSizeBytes;
+  return cached;
 }
 
 cudaError_t engine_launch(size_t smem, const EngineArgs& ea, int grid, cudaStream_t st) {

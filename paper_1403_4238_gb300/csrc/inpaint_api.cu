@@ -217,12 +217,14 @@ int tuned_rows_per_warp(const char* path, int r, long long pixels) {
   return out;
 }
 
-// Candidate rows per warp in a search batch (a batch is 16 warps x rows x
-// 128 columns): 2 when every CTA still gets about two batches, else 1.
+// Search batch width (a batch is 32 candidate rows x 16 warps x 4 * srw
+// candidate columns): srw = 2 (8 candidates per lane, the fewer loads per
+// evaluation) when that still gives every CTA of the team a batch, else 1.
 int pick_rows_per_warp(const ImgState& s, int grid) {
   const int xb = s.r + ((s.cx0 - s.r) & ~3);
-  const long long ncg = (s.cx1 - xb + 128) / 128, ch = s.cy1 - s.cy0 + 1;
-  return ncg * ((ch + 2 * kEngWarps - 1) / (2 * kEngWarps)) >= 2ll * grid ? 2 : 1;
+  const long long w2 = eng_batch_cols(2);
+  const long long ncg = (s.cx1 - xb + w2) / w2, ch = s.cy1 - s.cy0 + 1;
+  return ncg * ((ch + kEngBatchRows - 1) / kEngBatchRows) >= (long long)grid ? 2 : 1;
 }
 
 int setup_engine(inpaint_ctx* c) {
@@ -238,7 +240,12 @@ int setup_engine(inpaint_ctx* c) {
   const EngineFns* f = engine_fns(c->r);
   if (!f) return INPAINT_ERR_UNSUPPORTED;
   int bps = 0;
-  CK(engine_occupancy(f->smem_bytes(2), &bps));
+  const size_t smem = engine_launch_smem();
+  if (smem < f->smem_bytes(2)) {
+    g_last_error = "engine kernel does not fit on an SM";
+    return INPAINT_ERR_UNSUPPORTED;
+  }
+  CK(engine_occupancy(smem, &bps));
   if (bps < 1) {
     g_last_error = "engine kernel does not fit on an SM";
     return INPAINT_ERR_UNSUPPORTED;
@@ -246,10 +253,8 @@ int setup_engine(inpaint_ctx* c) {
   const int grid = sms * bps;
   if (!sr) sr = tuned_rows_per_warp(c->opt.tuning_file, c->r, (long long)c->W * c->H / grid);
   if (!sr) sr = pick_rows_per_warp(c->st, grid);
-  c->eng_smem = f->smem_bytes(sr);
-  CK(engine_occupancy(c->eng_smem, &bps));
-  const int g2 = sms * (bps < 1 ? 1 : bps);
-  c->eng_grid = g2 < grid ? g2 : grid;
+  c->eng_smem = smem;
+  c->eng_grid = grid;
   c->eng_sr = sr;
   c->st.srw = sr;
   if (!alloc_n(c, c->d_img, 1) || !alloc_n(c, c->d_tmap, 2) ||
@@ -928,10 +933,12 @@ int grid_for(const std::vector<inpaint_ctx*>& cs, int* grid) {
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  size_t smem_max = 0;
-  for (inpaint_ctx* c : cs) smem_max = std::max(smem_max, engine_fns(c->r)->smem_bytes(2));
+  size_t smem_min = 0;
+  for (inpaint_ctx* c : cs) smem_min = std::max(smem_min, engine_fns(c->r)->smem_bytes(2));
+  const size_t smem = engine_launch_smem();
+  if (smem < smem_min) return INPAINT_ERR_UNSUPPORTED;
   int bps = 0;
-  CK(engine_occupancy(smem_max, &bps));
+  CK(engine_occupancy(smem, &bps));
   if (bps < 1) return INPAINT_ERR_UNSUPPORTED;
   *grid = sms * bps;
   return INPAINT_OK;
@@ -963,8 +970,8 @@ int engine_set_prepare(EngineSet& es, const std::vector<inpaint_ctx*>& cs, const
       g_last_error = "cuTensorMapEncodeTiled failed";
       return INPAINT_ERR_CUDA;
     }
-    es.smem = std::max(es.smem, engine_fns(c->r)->smem_bytes(sr));
   }
+  es.smem = engine_launch_smem();
   std::vector<int> first(T + 1, 0), off(T + 1, 0), ints((size_t)G);
   std::vector<int> lst;
   for (int t = 0; t < T; ++t) {

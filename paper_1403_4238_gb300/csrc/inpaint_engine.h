@@ -9,7 +9,21 @@ namespace inp {
 
 constexpr int kEngThreads = 512;
 constexpr int kEngWarps = kEngThreads / 32;
-constexpr int kEngCountW = 132;  // count words staged per batch row (128 + alignment)
+constexpr int kEngBatchRows = 32;  // candidate rows of a search batch (one per lane)
+
+// Smallest staged width >= n words that is a multiple of 4 with an odd
+// number of 16-byte chunks: rows of a tile then start in different bank
+// quadruples, so 8 lanes reading 16 bytes each from 8 consecutive rows (one
+// phase of a 128-bit shared load) touch 32 distinct banks.
+__host__ __device__ constexpr int width_odd16(int n) {
+  return ((((n + 3) & ~3) / 4) % 2) ? ((n + 3) & ~3) : ((n + 3) & ~3) + 4;
+}
+// Candidate columns of a search batch: 16 warps side by side, 4 * srw
+// candidates per lane.
+__host__ __device__ constexpr int eng_batch_cols(int srw) { return kEngWarps * 4 * srw; }
+// TMA boxes of a batch: the source window (words) and the validity counts.
+__host__ __device__ constexpr int eng_tile_width(int r, int srw) { return width_odd16(eng_batch_cols(srw) + 2 * r); }
+__host__ __device__ constexpr int eng_count_width(int srw) { return eng_batch_cols(srw) + 4; }
 
 // Per-team synchronisation words (global memory).
 struct TeamCtl {
@@ -39,6 +53,7 @@ struct EngineArgs {
 // Per-CTA engine state carried from one image of a team's list to the next.
 struct EngCtx {
   uint8_t* smem;                // dynamic shared memory, 128-byte aligned
+  uint8_t* smem_end;            // end of the dynamic shared memory
   int rank, tsize;              // this CTA's rank in its team, team size
   TeamCtl* tc;
   unsigned long long* tpart;    // partial keys of the team's CTAs
@@ -64,7 +79,7 @@ INP_DECL_RUN_IMAGE(8)
 
 // Host-side entry points of one patch radius (engine_r<R>.cu).
 struct EngineFns {
-  size_t (*smem_bytes)(int srw);  // dynamic shared memory of the engine for this radius
+  size_t (*smem_bytes)(int srw);  // least dynamic shared memory the engine needs for this radius
   cudaError_t (*update_fast)(const ImgState& s, unsigned long long cond, int use_cond,
                              cudaStream_t st);
   cudaError_t (*prio_init)(const ImgState& s, cudaStream_t st);
@@ -79,9 +94,11 @@ const EngineFns* engine_fns_r7();
 const EngineFns* engine_fns_r8();
 
 const EngineFns* engine_fns(int r);
-// The engine kernel (engine_multi.cu); smem = the largest
-// engine_fns(r)->smem_bytes(srw) over the images of the launch.
+// The engine kernel (engine_multi.cu); every launch takes engine_launch_smem()
+// bytes, at least the largest engine_fns(r)->smem_bytes(srw) of its images.
 cudaError_t engine_occupancy(size_t smem, int* blocks_per_sm);
+// Dynamic shared memory of every engine launch: all an SM offers one CTA.
+size_t engine_launch_smem();
 cudaError_t engine_launch(size_t smem, const EngineArgs& ea, int grid, cudaStream_t st);
 int make_image_tmap(const ImgState& s, int srw, CUtensorMap* out);  // writes out[0], out[1]
 int make_image_tmap_box(const ImgState& s, int box_w, int box_h, CUtensorMap* out);

@@ -9,7 +9,8 @@ filter and a launch count:
     python -m paper_1403_4238_gb300.profile_cases search_plain_1080p --reps 3
 
 engine_*   whole removals (one persistent k_engine launch each, plus the
-           initialisation kernels), plain form;
+           initialisation kernels), plain form; --iters N stops each launch
+           after N iterations (a shorter launch for a full-counter capture);
 search_*   the findBestPatch kernel of one form alone, for the first target
            of the removal (inpaint_time_search), after one untimed launch.
 """
@@ -29,7 +30,7 @@ CASES = {
 }
 
 
-def run(name: str, reps: int):
+def run(name: str, reps: int, iters: int = 0):
     import torch
 
     make, kind, form = CASES[name]
@@ -39,9 +40,9 @@ def run(name: str, reps: int):
             drgb, dmask = torch.from_numpy(case.rgb).cuda(), torch.from_numpy(case.mask).cuda()
             for _ in range(reps):
                 ip.reset(drgb, dmask)
-                rc, n, _ = ip.run()
+                rc, n, _ = ip.run(max_iters=iters)
                 assert rc == 0, rc
-            print(f"{name}: {reps} removals of {n} iterations, {ip.info()['evals']} evals each")
+            print(f"{name}: {reps} launches of {n} iterations, {ip.info()['evals']} evals each")
     else:
         with api.Inpainter(case.rgb, case.mask, case.r, loop="graph") as ip:
             ms, key, ev = ip.time_search(form, reps)
@@ -52,8 +53,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=sorted(CASES))
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=0, help="engine cases: iterations per launch (0: all)")
     a = ap.parse_args()
-    run(a.case, a.reps)
+    run(a.case, a.reps, a.iters)
 
 
 if __name__ == "__main__":
