@@ -16,8 +16,8 @@ extern "C" {
 typedef struct {
   double ssd_evals_per_s; /* byte-SIMD abs-diff + 4-way byte dot product pairs per second
                              (one candidate-pixel SSD evaluation each), all SMs */
-  double imad_per_s;      /* 32-bit integer multiply-add per second, all SMs */
-  double iadd3_per_s;     /* dependent 32-bit integer adds per second, all SMs */
+  double imad_per_s;      /* 32-bit integer multiply-adds per second, all SMs */
+  double iadd3_per_s;     /* 32-bit three-input integer adds per second, all SMs */
   double dadd_per_s;      /* FP64 add per second, all SMs */
   double sm_clock_mhz;    /* SM clock seen during the probe (clock64 vs global timer) */
   int sm_count;
