@@ -1,21 +1,26 @@
-"""The allocation-free search entry point against the library's own search.
+"""The allocation-free search entry point, inpaint_best_patch_noalloc.
 
-inpaint_best_patch_noalloc serves callers that cannot allocate device memory
-(their memory is reserved up front by another framework, or they issue work
-while a stream is captured with a fixed memory plan).  Its result must be
-the one the regular entry point finds for the same target: the source patch
-and SSD that inpaint_step reports for its iteration, bit for bit.  Two calls
-in a row check that the shared static scratch carries nothing over between
-calls.  This file is collected last on purpose.
+It serves callers that cannot allocate device memory: their memory is
+reserved up front by another framework's allocator, or they issue work while
+a stream is captured into a graph with a fixed memory plan.  Its result must
+be the best patch of the search as the oracle defines it (Sec. 3, Eq. 3-4):
+the argmin of the oracle's SSD map over fully known in-image candidates,
+lowest linear index on ties, packed as (SSD << 32 | index), or UINT64_MAX
+when no candidate exists.  The cases cover one and several candidate tiles
+per row, radii 4, 6 and 8, a target on the image border, a target without
+any source, an image near the scratch limit, and two calls in a row (the
+shared static scratch must carry nothing over).  This file is collected last
+on purpose.
 """
-import ctypes
-
 import numpy as np
 import pytest
 
+import oracle
 from paper_1403_4238_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+KEY_NONE = (1 << 64) - 1
 
 
 @pytest.fixture(scope="module")
@@ -27,11 +32,11 @@ def env():
     return torch, _lib.load(), api
 
 
-def noalloc_key(torch, lib, rgb, mask, r, px, py):
+def noalloc_key(torch, lib, rgb, mask, r, px, py, prefill=-1):
     H, W = mask.shape
     d_rgb = torch.from_numpy(np.ascontiguousarray(rgb)).cuda()
     d_mask = torch.from_numpy(np.ascontiguousarray(mask)).cuda()
-    d_key = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    d_key = torch.full((1,), prefill, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     rc = lib.inpaint_best_patch_noalloc(d_rgb.data_ptr(), d_mask.data_ptr(), W, H, r, px, py,
                                         d_key.data_ptr(), stream)
@@ -40,7 +45,72 @@ def noalloc_key(torch, lib, rgb, mask, r, px, py):
     return int(d_key.cpu().numpy().view(np.uint64)[0])
 
 
-def test_noalloc_matches_regular_search_two_calls(env):
+def oracle_key(rgb, mask, r, px, py):
+    """Argmin of the oracle's SSD map (invalid candidates hold UINT32_MAX)."""
+    ssd, n_cand, _ = oracle.ssd_map(rgb, (mask != 0).astype(np.uint8), r, px, py)
+    if n_cand == 0:
+        return KEY_NONE
+    flat = ssd.ravel().astype(np.uint64)
+    valid = ssd.ravel() != np.uint32(0xFFFFFFFF)
+    idx = int(np.flatnonzero(valid)[np.argmin(flat[valid])])  # first minimum: lowest index
+    return (int(flat[idx]) << 32) | idx
+
+
+def first_target(case):
+    t = oracle.run(case.rgb, case.mask, case.r, max_iters=1).trace[0]
+    return int(t["px"]), int(t["py"])
+
+
+def ellipse_case(W, H, r, seed):
+    return synth.Case(f"ell{W}x{H}_r{r}", synth.image(W, H, 8, 30.0, seed),
+                      synth.ellipse_mask(W, H, 2, 0.03, 0.05, seed + 1), r)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.small_rect(seed=61),       # 128x96, r=4: one 128-column tile per row
+    lambda: synth.walkingman_like(),         # 512x384, r=4: four tiles per row
+    lambda: ellipse_case(300, 200, 6, 71),   # r=6
+    lambda: ellipse_case(240, 180, 8, 73),   # r=8, the largest radius of the entry point
+])
+def test_noalloc_equals_oracle_argmin(env, make):
+    torch, lib, _ = env
+    case = make()
+    px, py = first_target(case)
+    assert noalloc_key(torch, lib, case.rgb, case.mask, case.r, px, py) == \
+        oracle_key(case.rgb, case.mask, case.r, px, py)
+
+
+def test_noalloc_target_on_the_border(env):
+    torch, lib, _ = env
+    case = synth.tiny(60, 44, 9, hole=(0, 0, 7, 5), r=4)
+    for px, py in ((0, 0), (3, 0), (0, 4), (59, 43)):
+        assert noalloc_key(torch, lib, case.rgb, case.mask, case.r, px, py) == \
+            oracle_key(case.rgb, case.mask, case.r, px, py), (px, py)
+
+
+def test_noalloc_without_any_source_writes_key_none(env):
+    torch, lib, _ = env
+    W, H, r = 96, 72, 4
+    mask = np.zeros((H, W), np.uint8)
+    mask[r::2 * r, r::2 * r] = 1  # every (2r+1)^2 patch holds an unknown pixel
+    rgb = synth.image(W, H, 5, 30.0, 31)
+    assert oracle_key(rgb, mask, r, 20, 20) == KEY_NONE
+    # the output starts as another value: the kernel must write the result
+    assert noalloc_key(torch, lib, rgb, mask, r, 20, 20, prefill=0x1234) == KEY_NONE
+
+
+def test_noalloc_near_its_scratch_limit(env):
+    torch, lib, _ = env
+    # 2048 x 2048 with r = 4: 16 x 255 = 4080 candidate tiles of the 4096 allowed
+    W = H = 2048
+    rgb = synth.image(W, H, 6, 30.0, 81)
+    mask = np.zeros((H, W), np.uint8)
+    mask[1000:1012, 900:916] = 1
+    px, py = 900, 1005
+    assert noalloc_key(torch, lib, rgb, mask, 4, px, py) == oracle_key(rgb, mask, 4, px, py)
+
+
+def test_noalloc_two_calls_in_a_row_match_the_regular_search(env):
     torch, lib, api = env
     case = synth.small_rect(seed=61)
     H, W = case.mask.shape
@@ -54,6 +124,7 @@ def test_noalloc_matches_regular_search_two_calls(env):
         key = noalloc_key(torch, lib, rgb, om, case.r, int(rec["px"]), int(rec["py"]))
         want = (int(rec["ssd"]) << 32) | (int(rec["qy"]) * W + int(rec["qx"]))
         assert key == want, (hex(key), hex(want))
+        assert key == oracle_key(rgb, om, case.r, int(rec["px"]), int(rec["py"]))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(env):
