@@ -10,6 +10,7 @@ import ctypes
 import os
 import shutil
 import subprocess
+import sys
 import threading
 from concurrent.futures import ThreadPoolExecutor
 
@@ -25,8 +26,9 @@ LIB_PATH = os.path.join(OUT_DIR, "libinpaint.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [
     ARCH, "-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-rdc=true", "-maxrregcount=128",
-    "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC,
+    "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC, "-I", OUT_DIR,
 ]
+GENERATED = {"ssd_rows.cuh": "gen_ssd_rows.py"}  # headers written into OUT_DIR by csrc scripts
 
 _lock = threading.Lock()
 _lib = None
@@ -44,7 +46,7 @@ def sources():
 
 
 def _deps():
-    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h", ".py"))]
     hdrs += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return sources() + hdrs + [os.path.abspath(__file__)]
 
@@ -57,6 +59,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB_PATH
     nvcc = _nvcc()
     objs = []
+    for hdr, script in GENERATED.items():
+        p = subprocess.run([sys.executable, os.path.join(CSRC, script)], capture_output=True, text=True)
+        if p.returncode != 0:
+            raise RuntimeError(f"{script} failed:\n{p.stderr}")
+        with open(os.path.join(OUT_DIR, hdr), "w") as f:
+            f.write(p.stdout)
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")

@@ -19,6 +19,7 @@
 
 #include "inpaint_engine.h"
 #include "ptx.cuh"
+#include "ssd_rows.cuh"
 #include "update_fast.cuh"
 
 namespace inp {
@@ -199,30 +200,159 @@ __device__ __noinline__ unsigned long long unit_best(const uint32_t* strip, cons
   return best;
 }
 
-// All units of a CTA whose batches are resident: slot i holds batch
-// rank + i * ns of the image (tile, then the validity bits per (warp, lane)).
-template <int R, int SRW>
-__device__ __noinline__ unsigned long long resident_units(const uint8_t* slots, int nmine, int rank, int ns,
-                                                          int ncg, int xb, int cy0, int W,
-                                                          const uint32_t* tgt, const uint32_t* rowd) {
-  using G = EngGeom<R, SRW>;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long best = ~0ull;
-#pragma unroll 1
-  for (int i = 0; i < nmine; ++i) {
-    const int b = rank + i * ns, gx = b % ncg, gy = b / ncg;
-    const uint8_t* slot = slots + (size_t)i * G::SLOT_BYTES;
-    const uint32_t bits = slot[G::PIX_BYTES + warp * 32 + lane];
-    const unsigned idx0 = (unsigned)((cy0 + G::B * gy + lane) * W + xb + G::BWC * gx + G::NCL * warp);
-    uint32_t acc[G::NCL];
-    unit_ssd<R, SRW>(reinterpret_cast<const uint32_t*>(slot) + lane * G::BW + G::NCL * warp, tgt, rowd, acc);
+// ---------------------------------------------------------------- resident search
+
+// Resident mode: the candidate rectangle is cut into units of 32 candidate
+// rows (one per lane) x 16 candidate columns (one lane's candidates); the
+// units, in band-major order, are split into contiguous ranges of equal
+// size, one per searching CTA.  A CTA keeps the source window of its units
+// in shared memory for the whole removal (one tile per 32-row band its range
+// touches) and after each publication only patches the pixels the previous
+// iteration filled and the validity of the candidates near them.
+constexpr int kResCols = 16;   // candidates per lane
+constexpr int kResRows = 32;   // candidate rows per unit (one per lane)
+constexpr int kResMaxSeg = 4;  // bands one CTA's tiles may span
+
+struct ResSeg {
+  int band;      // 32-row band of the search rectangle
+  int c_lo;      // first unit column of the band in this CTA's range
+  int pitch;     // tile row pitch (words), pitch / 4 odd
+  int off;       // byte offset of the tile in the CTA's tile area
+};
+
+struct ResPlan {
+  int u0, u1;        // this CTA's units [u0, u1), band-major
+  int ncu;           // unit columns per band
+  int nseg;
+  int bits_off;      // byte offset of the validity bits (uint16 per unit and lane)
+  ResSeg seg[kResMaxSeg];
+};
+
+template <int R>
+struct ResGeom {
+  static constexpr int P = 2 * R + 1;
+  static constexpr int NS = (kResCols + P - 1 + 3) & ~3;  // strip words per lane
+  static constexpr int TP = (P + 3) & ~3;
+  static constexpr int TH = kResRows + 2 * R;             // tile rows
+};
+
+// SSD of this lane's 16 candidates (Eq. 4) for one unit: per target row one
+// indexed jump into the row sequences of ssd_rows.cuh (known run [s, P) or
+// [0, e)); other row shapes test a bit per column.
+template <int R>
+__device__ __forceinline__ void unit16_ssd(const uint32_t* __restrict__ strip, int pitch,
+                                           const uint32_t* __restrict__ tgt,
+                                           const uint32_t* __restrict__ rowd, uint32_t (&acc)[kResCols]) {
+  using G = ResGeom<R>;
+  constexpr int P = G::P, NS = G::NS, TP = G::TP;
 #pragma unroll
-    for (int k = 0; k < G::NCL; ++k) {
-      const unsigned long long key = ((unsigned long long)acc[k] << 32) | (idx0 + (unsigned)k);
-      if ((bits & (1u << k)) && key < best) best = key;
+  for (int k = 0; k < kResCols; ++k) acc[k] = 0;
+#pragma unroll 1
+  for (int dy = 0; dy < P; ++dy) {
+    const uint32_t desc = rowd[dy];
+    if (desc == kRowSkip) continue;
+    uint32_t r[NS], t[TP];
+    lds_words(r, strip + dy * pitch);
+    lds_words(t, tgt + dy * G::TP);
+    const uint32_t kind = desc & (3u << 30);
+    if (kind != kRowMask) {
+      const uint32_t arg = desc & 0xffffu;
+      // entry of the jump table: [0, P) ascending from column s, [P, 2P)
+      // descending from column e - 1; clamped so that it stays in the table
+      const uint32_t idx = min(kind == kRowFrom ? arg : (uint32_t)P + arg - 1u, (uint32_t)(2 * P - 1));
+      if constexpr (P == 3) INP_SSD_ROW16_P3(acc, r, t, idx);
+      if constexpr (P == 5) INP_SSD_ROW16_P5(acc, r, t, idx);
+      if constexpr (P == 7) INP_SSD_ROW16_P7(acc, r, t, idx);
+      if constexpr (P == 9) INP_SSD_ROW16_P9(acc, r, t, idx);
+      if constexpr (P == 11) INP_SSD_ROW16_P11(acc, r, t, idx);
+      if constexpr (P == 13) INP_SSD_ROW16_P13(acc, r, t, idx);
+      if constexpr (P == 15) INP_SSD_ROW16_P15(acc, r, t, idx);
+      if constexpr (P == 17) INP_SSD_ROW16_P17(acc, r, t, idx);
+    } else {
+#pragma unroll
+      for (int dx = 0; dx < P; ++dx) {
+        if (desc & (1u << dx)) {
+#pragma unroll
+          for (int k = 0; k < kResCols; ++k) {
+            const uint32_t d = __vabsdiffu4(t[dx], r[k + dx]);
+            acc[k] = __dp4a(d, d, acc[k]);
+          }
+        }
+      }
     }
   }
+}
+
+// Smallest key (SSD << 32 | idx) of this lane's 16 candidates of one unit:
+// `vb` marks the valid ones, idx0 is the linear index of the first.
+template <int R>
+__device__ __noinline__ unsigned long long unit16_best(const uint32_t* strip, int pitch, const uint32_t* tgt,
+                                                       const uint32_t* rowd, uint32_t vb, unsigned idx0) {
+  uint32_t acc[kResCols];
+  unit16_ssd<R>(strip, pitch, tgt, rowd, acc);
+  unsigned long long best = ~0ull;
+#pragma unroll
+  for (int k = 0; k < kResCols; ++k) {
+    const unsigned long long key = ((unsigned long long)acc[k] << 32) | (idx0 + (unsigned)k);
+    if ((vb & (1u << k)) && key < best) best = key;
+  }
   return best;
+}
+
+// All units of this CTA for the current target, warp w taking its local
+// units w, w + 16, ...; returns the lane's smallest key.
+template <int R>
+__device__ __noinline__ unsigned long long resident_units16(const ResPlan* pl, const uint8_t* tiles, int xb,
+                                                            int cy0, int W, const uint32_t* tgt,
+                                                            const uint32_t* rowd) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int u0 = pl->u0, n = pl->u1 - pl->u0, ncu = pl->ncu, b0 = pl->seg[0].band;
+  const uint16_t* bits = reinterpret_cast<const uint16_t*>(tiles + pl->bits_off);
+  unsigned long long best = ~0ull;
+#pragma unroll 1
+  for (int j = warp; j < n; j += kEngWarps) {
+    const int u = u0 + j, band = u / ncu, col = u - band * ncu;
+    const ResSeg& sg = pl->seg[band - b0];
+    const uint32_t* strip = reinterpret_cast<const uint32_t*>(tiles + sg.off) + lane * sg.pitch +
+                            (col - sg.c_lo) * kResCols;
+    const unsigned idx0 = (unsigned)((cy0 + band * kResRows + lane) * W + xb + col * kResCols);
+    const unsigned long long k = unit16_best<R>(strip, sg.pitch, tgt, rowd, bits[j * 32 + lane], idx0);
+    best = k < best ? k : best;
+  }
+  return best;
+}
+
+// Plan of rank `rank`'s units: the tile of each band its range touches.
+// Returns the bytes of shared memory the plan needs (tiles + validity
+// bits), or -1 when the range spans more bands than kResMaxSeg.
+template <int R>
+__host__ __device__ inline long long res_plan(ResPlan& pl, int ncu, int nbands, int rank, int ns) {
+  using G = ResGeom<R>;
+  const long long U = (long long)ncu * nbands;
+  pl.u0 = (int)(U * rank / ns);
+  pl.u1 = (int)(U * (rank + 1) / ns);
+  pl.ncu = ncu;
+  pl.nseg = 0;
+  if (pl.u1 <= pl.u0) {
+    pl.bits_off = 0;
+    return 0;
+  }
+  const int b_lo = pl.u0 / ncu, b_hi = (pl.u1 - 1) / ncu;
+  if (b_hi - b_lo + 1 > kResMaxSeg) return -1;
+  long long off = 0;
+  for (int b = b_lo; b <= b_hi; ++b) {
+    const int c_lo = b == b_lo ? pl.u0 % ncu : 0;
+    const int c_hi = b == b_hi ? (pl.u1 - 1) % ncu + 1 : ncu;
+    ResSeg& sg = pl.seg[pl.nseg++];
+    sg.band = b;
+    sg.c_lo = c_lo;
+    sg.pitch = width_odd16((c_hi - c_lo) * kResCols + 2 * R);
+    sg.off = (int)off;
+    off += (((long long)sg.pitch * G::TH * 4) + 127) / 128 * 128;
+  }
+  pl.bits_off = (int)off;
+  off += (long long)(pl.u1 - pl.u0) * 32 * 2;
+  return off;
 }
 
 // ---------------------------------------------------------------- kernel
@@ -236,6 +366,7 @@ struct EngSmemTail {
   int stop;
   int px, py;
   uint8_t known[2][17 * 17];  // known flags of the last two targets (by round parity)
+  ResPlan plan;               // resident mode: this CTA's units and tiles
 };
 
 constexpr int kTgtWords = 17 * 20 + 17 + 3;  // padded target rows + row masks (R <= 8)
@@ -308,7 +439,6 @@ __device__ inline unsigned long long wait_pub(TeamCtl* tc, unsigned epoch, int* 
   if ((unsigned)v != epoch) return v;
   const unsigned long long t0 = globaltimer();
   while (true) {
-    __nanosleep(20);
     v = ld_acquire64(&tc->pub);
     if ((unsigned)v != epoch) return v;
     if (globaltimer() - t0 > limit) {
@@ -358,6 +488,7 @@ __device__ __noinline__ void run_lead_only(const EngineArgs& ea, int j, EngCtx& 
 template <int R, int SRW, bool kLeadOnly>
 __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x) {
   using G = EngGeom<R, SRW>;
+  using RG = ResGeom<R>;
   constexpr int P = G::P, B = G::B;
   uint8_t* smem = x.smem;
   EngSmemTail& tl = *reinterpret_cast<EngSmemTail*>(smem);
@@ -407,19 +538,38 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       return;
     }
   }
-  // count tiles and slots (a searching leader keeps its update state below them)
+  // the CTA's work area (a searching leader keeps its update state below it)
   uint8_t* area = smem + kHeadBytes + (leader ? ((upd_smem_bytes<R>() + 127) / 128) * 128 : 0);
+  // streaming mode: two count tiles and two tile slots (double buffer)
   uint32_t* cnt_t[2] = {reinterpret_cast<uint32_t*>(area),
                         reinterpret_cast<uint32_t*>(area + G::CNT_BYTES)};
   uint8_t* slots = area + 2 * G::CNT_BYTES;
-  const int nslots = (int)((x.smem_end - slots) / G::SLOT_BYTES);
-  const int nmine = rank < ns ? (nbatch - rank + ns - 1) / ns : 0;  // batches rank, rank + ns, ...
-  // every batch of this CTA keeps its tile in a slot of its own across the
-  // iterations; the filled pixels and the validity of the candidates near
-  // each target are refreshed after the publication instead of a reload
-  const bool resident = nmine >= 1 && nmine <= nslots;
   auto slot_pix = [&](int i) { return reinterpret_cast<uint32_t*>(slots + (size_t)i * G::SLOT_BYTES); };
-  auto slot_vb = [&](int i) { return slots + (size_t)i * G::SLOT_BYTES + G::PIX_BYTES; };
+  // resident mode when every searching CTA's tiles fit (the same decision
+  // in every CTA of the team: the bound below depends only on the image,
+  // the team and the smallest work area, a searching leader's)
+  const int ncu = s.cx1 >= s.cx0 ? (s.cx1 - xb + kResCols) / kResCols : 0;
+  const int nbands = s.cy1 >= s.cy0 ? (s.cy1 - s.cy0 + kResRows) / kResRows : 0;
+  bool resident = false;
+  {
+    const long long U = (long long)ncu * nbands;
+    const long long m = ns > 0 ? (U + ns - 1) / ns : 0;  // most units of one CTA
+    const long long avail =
+        (long long)(x.smem_end - (smem + kHeadBytes)) -
+        (lead_searches ? ((long long)(upd_smem_bytes<R>() + 127) / 128) * 128 : 0);
+    // two tiles (a range may straddle a band boundary) plus the bits; more
+    // than one band of units per CTA streams instead
+    const long long need = (long long)(kResRows + 2 * R) * 4 *
+                               (m * kResCols + 2 * (2 * R + 8)) + 256 + m * 64;
+    // at least half a unit per warp, else the batches of the streaming
+    // mode spread the search over more warps
+    resident = m >= kEngWarps / 2 && m <= ncu && need <= avail;
+  }
+  ResPlan& pl = tl.plan;
+  if (resident && searcher) {
+    if (tid == 0) res_plan<R>(pl, ncu, nbands, rank, ns);
+    __syncthreads();
+  }
   if (tid == 0) {
     tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
     tl.px = __ldcg(&c->px);
@@ -446,47 +596,52 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       tma_load_2d(ct, cmap, xb - G::COFF + G::BWC * gx, s.cy0 + B * gy, bar);
     };
     const bool first = round == 0;
-    if (resident) {
-      if (first && tid == 0) {
-        // every tile of the CTA at once
-        mbar_expect_tx(&tl.full[0], (uint32_t)(nmine * G::BW * G::BH * 4));
-        for (int i = 0; i < nmine; ++i) {
-          const int b = rank + i * ns, gx = b % ncg, gy = b / ncg;
-          tma_load_2d(slot_pix(i), map, xb - R + G::BWC * gx, s.cy0 + B * gy - R, &tl.full[0]);
+    if (!resident && tid == 0 && b0 < nbatch) issue(b0, slot_pix(0), cnt_t[0], &tl.full[0]);
+    const uint8_t* tiles = area;
+    if (resident && first) {
+      // the source windows of every band segment (plain 16-byte loads;
+      // outside the image: zero), then the validity bits of every unit
+      for (int g = 0; g < pl.nseg; ++g) {
+        const ResSeg sg = pl.seg[g];
+        const int x0 = xb - R + sg.c_lo * kResCols, y0 = s.cy0 + sg.band * kResRows - R;
+        const int nq = sg.pitch / 4;
+        uint4* dst = reinterpret_cast<uint4*>(area + sg.off);
+        for (int i = tid; i < RG::TH * nq; i += kEngThreads) {
+          const int row = i / nq, q = i - row * nq, y = y0 + row, xw = x0 + 4 * q;
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (y >= 0 && y < s.H && xw + 3 < s.pitch)
+            v = __ldcg(reinterpret_cast<const uint4*>(s.img + (size_t)y * s.pitch + xw));
+          dst[i] = v;
         }
       }
-    } else if (tid == 0 && b0 < nbatch) {
-      issue(b0, slot_pix(0), cnt_t[0], &tl.full[0]);
-    }
-    if (resident && first) {
-      // validity bits of every candidate of the CTA's batches
-      for (int i = 0; i < nmine; ++i) {
-        const int b = rank + i * ns, gx = b % ncg, gy = b / ncg;
-        const int qy = s.cy0 + B * gy + lane, qx0 = xb + G::BWC * gx + G::NCL * warp;
-        uint32_t bits = 0;
+      uint16_t* bits = reinterpret_cast<uint16_t*>(area + pl.bits_off);
+      for (int jj = warp; jj < pl.u1 - pl.u0; jj += kEngWarps) {
+        const int u = pl.u0 + jj, band = u / ncu, col = u - band * ncu;
+        const int qy = s.cy0 + band * kResRows + lane, qx0 = xb + col * kResCols;
+        uint32_t v = 0;
         if (qy <= s.cy1) {
 #pragma unroll
-          for (int k = 0; k < G::NCL; ++k) {
+          for (int k = 0; k < kResCols; ++k) {
             const int qx = qx0 + k;
-            if (qx >= s.cx0 && qx <= s.cx1 && __ldcg(&s.count[(size_t)qy * s.pitch + qx]) == 0)
-              bits |= 1u << k;
+            if (qx >= s.cx0 && qx <= s.cx1 && __ldcg(&s.count[(size_t)qy * s.pitch + qx]) == 0) v |= 1u << k;
           }
         }
-        slot_vb(i)[warp * 32 + lane] = (uint8_t)bits;
+        bits[jj * 32 + lane] = (uint16_t)v;
       }
-    } else if (resident) {
+    } else if (resident && pl.u1 > pl.u0) {
       // the previous target's filled pixels (its unknown in-image pixels),
-      // copied by the leader before the publication, into every tile
-      // window that holds them
+      // copied by the leader before the publication, into every tile that
+      // holds them
       const uint8_t* kprev = tl.known[par ^ 1];
       if (tid < P * P) {
         const int tx = prev_px + tid % P - R, ty = prev_py + tid / P - R;
         if (tx >= 0 && tx < s.W && ty >= 0 && ty < s.H && !kprev[tid]) {
           const uint32_t w = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
-          for (int i = 0; i < nmine; ++i) {
-            const int b = rank + i * ns, gx = b % ncg, gy = b / ncg;
-            const int lx = tx - (xb - R + G::BWC * gx), ly = ty - (s.cy0 + B * gy - R);
-            if (lx >= 0 && lx < G::BW && ly >= 0 && ly < G::BH) slot_pix(i)[ly * G::BW + lx] = w;
+          for (int g = 0; g < pl.nseg; ++g) {
+            const ResSeg& sg = pl.seg[g];
+            const int lx = tx - (xb - R + sg.c_lo * kResCols), ly = ty - (s.cy0 + sg.band * kResRows - R);
+            if (lx >= 0 && lx < sg.pitch && ly >= 0 && ly < RG::TH)
+              reinterpret_cast<uint32_t*>(area + sg.off)[ly * sg.pitch + lx] = w;
           }
         }
       }
@@ -495,12 +650,13 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       for (int jj = tid; jj < NCW * NCW; jj += kEngThreads) {
         const int qx = prev_px + jj % NCW - 2 * R, qy = prev_py + jj / NCW - 2 * R;
         if (qx < s.cx0 || qx > s.cx1 || qy < s.cy0 || qy > s.cy1) continue;
-        const int gx = (qx - xb) / G::BWC, gy = (qy - s.cy0) / B, b = gy * ncg + gx;
-        if (b % ns != rank) continue;
+        const int band = (qy - s.cy0) / kResRows, col = (qx - xb) / kResCols;
+        const int u = band * ncu + col;
+        if (u < pl.u0 || u >= pl.u1) continue;
         if (__ldcg(&s.count[(size_t)qy * s.pitch + qx]) != 0) continue;
-        const int cx = (qx - xb) % G::BWC, e = (cx / G::NCL) * 32 + (qy - s.cy0) % B;
-        uint8_t* vb = slot_vb((b - rank) / ns);
-        atomicOr(reinterpret_cast<unsigned*>(vb + (e & ~3)), (1u << (cx % G::NCL)) << (8 * (e & 3)));
+        const int e = (u - pl.u0) * 32 + (qy - s.cy0) % kResRows;
+        atomicOr(reinterpret_cast<unsigned*>(area + pl.bits_off) + (e >> 1),
+                 (1u << ((qx - xb) % kResCols)) << (16 * (e & 1)));
       }
     }
     // target patch: warp dy reads row dy (lane = dx); the ballot of the
@@ -530,12 +686,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     unsigned long long best = ~0ull;
     bool ok = true;
     if (resident) {
-      if (first) {
-        ok = mbar_wait(&tl.full[0], ph0, limit);
-        ph0 ^= 1;
-      }
-      if (ok) best = resident_units<R, SRW>(slots, nmine, rank, ns, ncg, xb, s.cy0, s.W, tgt, rowd);
-      ok = !__syncthreads_or(!ok);
+      if (pl.u1 > pl.u0) best = resident_units16<R>(&pl, tiles, xb, s.cy0, s.W, tgt, rowd);
     } else {
       int cur = 0;
       for (int b = b0; b < nbatch; b += ns) {
