@@ -4,13 +4,17 @@
 // CTAs form teams; a team runs the fill loop of one image at a time (a list
 // of images per team gives the batched form).  One iteration of a team:
 //   1. every member CTA searches its share of the candidate centres
-//      (findBestPatch, Eq. 3-4): per warp, a unit of SR candidate rows x 128
-//      candidate columns whose (SR+2R) x (128+2R) source window is brought
-//      into shared memory by a TMA tile load, double-buffered, and reduced
-//      to one (SSD << 32 | idx) key;
-//   2. each member writes its key and arrives on the team counter; the last
-//      to arrive runs the copy/update phase and the selection of the next
-//      target (update_fast.cuh) and publishes the next epoch;
+//      (findBestPatch, Eq. 3-4).  Resident mode (large images): the CTA
+//      owns a contiguous range of units of 32 candidate rows x 16 columns,
+//      keeps their source window in shared memory for the whole removal and
+//      only patches the pixels the previous iteration filled; streaming
+//      mode (small images, small teams): batches of 32 rows x 64 or 128
+//      columns whose source window and validity counts arrive by TMA,
+//      double-buffered.  Each lane owns the candidates of one row; the
+//      CTA reduces them to one (SSD << 32 | idx) key;
+//   2. each member writes its key, tagged with the round, to its slot; the
+//      leader polls the slots, runs the copy/update phase and the selection
+//      of the next target (update_fast.cuh) and publishes the next epoch;
 //   3. the others wait for that epoch (bounded wait, no trap) and go on.
 // No host round trip and no kernel boundary per iteration.
 #pragma once
@@ -362,6 +366,7 @@ struct EngSmemTail {
   ImgState img;      // the image's state block (a leader that does not search reads it here)
   unsigned long long red64[32];
   int red32[32];
+  unsigned long long key;  // best key of the round (leader)
   int flag;
   int stop;
   int px, py;
@@ -427,9 +432,6 @@ __device__ inline void st_relaxed64(unsigned long long* p, unsigned long long v)
 // tile to scan in most iterations, so that its fence waits off the path.
 constexpr int kPubThread = kEngThreads - 1;
 
-__device__ inline void red_release_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Bounded wait (thread 0) for a publication with an epoch other than `epoch`;
 // returns it, or a stop word after setting *err on timeout.
@@ -448,16 +450,56 @@ __device__ inline unsigned long long wait_pub(TeamCtl* tc, unsigned epoch, int* 
   }
 }
 
-// Bounded wait (thread 0) until `n` searchers arrived; false on timeout.
-__device__ inline bool wait_arrivals(TeamCtl* tc, unsigned n, int* err, unsigned long long limit) {
-  if (ld_acquire(&tc->arrive) >= n) return true;
-  const unsigned long long t0 = globaltimer();
-  while (ld_acquire(&tc->arrive) < n) {
-    if (globaltimer() - t0 > limit) {
-      atomicExch(err, INPAINT_ERR_TIMEOUT);
-      return false;
+// A searcher's best key of a round travels to the leader tagged with the
+// round: (SSD << 38) | (idx << 8) | tag, tag = epoch mod 128 (SSD < 2^26 for
+// radius <= 8, idx < 2^30), so the leader polls the keys themselves and no
+// separate arrival counter is needed.  Keys of one round carry the same tag,
+// so the tagged values order like (SSD, idx).  Slots are set to all ones
+// (tag 0xff, never a round's) before every launch.
+__device__ inline unsigned long long key_tag(unsigned long long key, unsigned epoch) {
+  if (key == ~0ull) return ~0ull & ~0xffull | (epoch & 0x7fu);
+  return ((key >> 32) << 38) | ((key & 0x3fffffffull) << 8) | (epoch & 0x7fu);
+}
+
+__device__ inline unsigned long long key_untag(unsigned long long t) {
+  const unsigned long long ssd = t >> 38, idx = (t >> 8) & 0x3fffffffull;
+  if (ssd == 0x3ffffffull && idx == 0x3fffffffull) return ~0ull;
+  return (ssd << 32) | idx;
+}
+
+// Leader: the best key of the round over the tagged slots [0, n), each
+// polled (bounded) by one thread until it carries the round's tag; the
+// untagged minimum lands in *out.  Returns false (every thread) when a
+// slot did not arrive in time.  Whole block; ends with a __syncthreads.
+__device__ inline bool gather_keys(const unsigned long long* slots, int n, unsigned epoch, int* err,
+                                   unsigned long long limit, unsigned long long* red,
+                                   unsigned long long* out) {
+  unsigned long long best = ~0ull;
+  bool late = false;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    unsigned long long v = ld_acquire64(&slots[i]);
+    if ((v & 0xffu) != (epoch & 0x7fu)) {
+      const unsigned long long t0 = globaltimer();
+      do {
+        v = ld_acquire64(&slots[i]);
+        if (globaltimer() - t0 > limit) {
+          late = true;
+          break;
+        }
+      } while ((v & 0xffu) != (epoch & 0x7fu));
+    }
+    if (!late) {
+      const unsigned long long k = key_untag(v);
+      best = k < best ? k : best;
     }
   }
+  if (__syncthreads_or(late)) {
+    if (threadIdx.x == 0) atomicExch(err, INPAINT_ERR_TIMEOUT);
+    return false;
+  }
+  best = block_min_u64(best, red);
+  if (threadIdx.x == 0) *out = best;
+  __syncthreads();
   return true;
 }
 
@@ -531,7 +573,6 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   const int ns = lead_searches ? tsize : min(tsize - 1, nbatch);
   const bool leader = rank == tsize - 1;
   const bool searcher = rank < ns;
-  const unsigned n_wait = (unsigned)(lead_searches ? ns - 1 : ns);
   if constexpr (!kLeadOnly) {
     if (leader && !searcher) {
       run_lead_only<R, SRW>(ea, j, x);
@@ -742,19 +783,15 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     spec_phase<R>(s, usm, uca, staged);
     if (searches) {
       const unsigned long long best = search_round(px, py);
-      if (tid == 0) tpart[rank] = best;
+      if (tid == 0) st_release64(&tpart[rank], key_tag(best, epoch));
     }
-    if (tid == 0) {
-      tl.flag = wait_arrivals(tc, n_wait, ea.err, limit);
-      tc->arrive = 0u;  // all keys are in; ordered before the next publication by its fence
-    }
-    __syncthreads();
+    tl.flag = gather_keys(tpart, ns, epoch, ea.err, limit, tl.red64, &tl.key);
     bool stop = true, ok = false;
     int npx = 0, npy = 0;
     unsigned long long t_b = 0ull;
     if (tl.flag) {
       t_b = globaltimer();
-      ok = update_phase<R>(s, tpart, ns, usm, uca, kPubThread);  // ends with a __syncthreads
+      ok = update_phase<R>(s, nullptr, 0, usm, uca, kPubThread, false, &tl.key);  // ends with a __syncthreads
       if (ok) {
         // the next target is known: publish it before the bookkeeping.
         // Thread 0 decides (the inputs are global and may change under
@@ -818,10 +855,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     }
     if (searcher) {
       const unsigned long long best = search_round(px, py);
-      if (tid == 0) {
-        tpart[rank] = best;
-        if (rank + 1 != ea.withhold) red_release_add(&tc->arrive, 1u);
-      }
+      if (tid == 0 && rank + 1 != ea.withhold) st_release64(&tpart[rank], key_tag(best, epoch));
     }
     // searchers and idle CTAs: wait for the next round
     if (tid == 0) {

@@ -86,6 +86,9 @@ size_t engine_launch_smem() {
 cudaError_t engine_launch(size_t smem, const EngineArgs& ea, int grid, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // key slots: all ones (a tag no round carries) before the launch
+  e = cudaMemsetAsync(ea.partials, 0xff, sizeof(unsigned long long) * (size_t)grid, st);
+  if (e != cudaSuccess) return e;
   void* args[] = {const_cast<EngineArgs*>(&ea)};
   return cudaLaunchCooperativeKernel((const void*)k_engine, dim3(grid), dim3(kEngThreads), args, smem, st);
 }

@@ -28,9 +28,8 @@ __host__ __device__ constexpr int eng_count_width(int srw) { return eng_batch_co
 // Per-team synchronisation words (global memory).
 struct TeamCtl {
   unsigned long long pub;  // epoch | next px | next py | stop (release-published)
-  unsigned arrive;         // searchers arrived in the current iteration
   unsigned expired;        // the launch's time budget ended this team's work
-  unsigned pad[28];        // keep teams on separate 128-byte lines
+  unsigned pad[29];        // keep teams on separate 128-byte lines
 };
 
 struct EngineArgs {
@@ -41,7 +40,7 @@ struct EngineArgs {
   const int* team_img_off;     // [n_teams + 1] offsets into team_img
   const int* team_img;         // images of each team, in processing order
   TeamCtl* teams;              // [n_teams]
-  unsigned long long* partials;// [grid]
+  unsigned long long* partials;// [grid] each CTA's best key of the round, tagged with the round
   int* err;                    // INPAINT_ERR_TIMEOUT if a bounded wait gave up
   unsigned long long wait_limit_ns;
   unsigned long long tick_ns;  // > 0: teams stop between iterations once the launch

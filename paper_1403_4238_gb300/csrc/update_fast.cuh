@@ -498,8 +498,8 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
   __syncthreads();
 }
 
-// Update phase: applies the iteration whose best source key is the minimum
-// of partial[0..n_partial), on the state prepared by spec_phase and
+// Update phase: applies the iteration whose best source key is *best_in, or
+// the minimum of partial[0..n_partial), on the state prepared by spec_phase and
 // update_prefetch.  Returns false (status written) when there is no source
 // patch or the state is inconsistent.  Whole block; ends with a __syncthreads.
 // Thread `fence_thread` (if any) issues a gpu-scope fence once the pixel,
@@ -509,7 +509,7 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
 template <int R>
 __device__ bool update_phase(const ImgState& s, const unsigned long long* partial, int n_partial,
                              UpdSmem<R>& sm, UpdCache<R>& ca, int fence_thread = -1,
-                             bool overlap_counts = false) {
+                             bool overlap_counts = false, const unsigned long long* best_in = nullptr) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW, NC = G::NC;
   Ctrl* c = s.ctrl;
@@ -522,13 +522,18 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const int n_cand = overlap_counts ? __ldcg(&c->n_adm) : __ldcg(&c->n_valid), it = __ldcg(&c->iter);
   int remaining = __ldcg(&c->remaining);
 
-  // best source key
+  // best source key: given (already reduced, in shared memory), or the
+  // minimum of the partial keys in global memory
   unsigned long long best = ~0ull;
-  for (int i = tid; i < n_partial; i += nt) {
-    const unsigned long long v = __ldcg(&partial[i]);
-    best = v < best ? v : best;
+  if (best_in) {
+    best = *best_in;
+  } else {
+    for (int i = tid; i < n_partial; i += nt) {
+      const unsigned long long v = __ldcg(&partial[i]);
+      best = v < best ? v : best;
+    }
+    best = block_min_u64(best, sm.red64);
   }
-  best = block_min_u64(best, sm.red64);
   if (best == ~0ull) {
     if (tid == 0) c->status = INPAINT_ERR_NO_SOURCE;
     __syncthreads();
