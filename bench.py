@@ -236,7 +236,7 @@ INT32_OPS_PER_EVAL = 6
 # launch and the digest of the kernel sources the capture was taken on.
 ENGINE_PROFILE = os.path.join(ROOT, "profiles", "k_engine_1920x1080.md")
 ENGINE_SOURCES = ("engine_impl.cuh", "engine_multi.cu", "update_fast.cuh", "inpaint_engine.h",
-                  "inpaint_internal.cuh", "ptx.cuh")
+                  "inpaint_internal.cuh", "ptx.cuh", "gen_ssd_rows.py")
 
 
 def engine_source_digest() -> str:

@@ -29,3 +29,17 @@ def test_two_rank_dry_run_reports_both_ranks_and_a_full_split():
     flat = sorted(i for share in d["batch_shares"] for i in share)
     assert flat == list(range(64))
     assert all(len(s) > 0 for s in d["batch_shares"])
+
+
+def test_engine_traffic_is_read_from_the_committed_capture():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    traffic, note = bench.engine_traffic()
+    with open(bench.ENGINE_PROFILE) as f:
+        text = f.read()
+    assert "traffic_bytes_per_launch:" in text and "sources_digest:" in text
+    if "sources" in note and "changed" not in note:
+        assert traffic and traffic > 0
+    else:
+        assert traffic is None  # stale capture: reported as null, with the reason
