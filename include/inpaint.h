@@ -85,14 +85,18 @@ typedef struct {
                             the whole loop (patch_radius <= 8 only);
                             INPAINT_LOOP_GRAPH: a CUDA graph with a conditional while
                             node around [search kernel, update kernel] */
-  int tile_rows;         /* engine search: candidate rows per warp in a search batch
-                            (a batch is 16 warps x rows x 128 candidate columns):
-                            1 or 2; 0 = chosen by the library */
+  int tile_rows;         /* engine search, streaming mode (small images or small
+                            teams): a search batch is 32 candidate rows (one per lane)
+                            x 16 warps x 4 * tile_rows candidate columns per lane,
+                            i.e. 64 (tile_rows = 1) or 128 (tile_rows = 2) columns;
+                            0 = chosen by the library.  Large images on large teams
+                            use the resident mode (units of 32 rows x 16 columns,
+                            source tiles kept in shared memory), whatever this is */
   const char* tuning_file; /* NULL, or a text table written by the autotuner: one line
-                            "radius max_pixels rows_per_warp" per bucket; the first
-                            line with the image's radius and max_pixels >= the image's
+                            "radius max_pixels tile_rows" per bucket; the first line
+                            with the image's radius and max_pixels >= the image's
                             pixels per CTA of its team (W*H / CTAs working on it)
-                            gives rows_per_warp when tile_rows is 0 */
+                            gives tile_rows when tile_rows is 0 */
   int search_variant;    /* INPAINT_SEARCH_FULL (default): candidate patches lie inside
                             the image and inside the known region (Eq. 3-4);
                             INPAINT_SEARCH_OVERLAP: the partial-overlap variant of

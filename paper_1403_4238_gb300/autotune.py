@@ -1,8 +1,8 @@
-"""Autotuner for the engine's search batch shape.
+"""Autotuner for the engine's search batch shape (streaming mode).
 
-A search batch is 16 warps x rows x 128 candidate columns; with 1 row per
-warp each lane keeps 4 candidates of one row, with 2 rows the half-warps
-take two rows and each lane 8 candidates (cheaper per evaluation, but
+A search batch is 32 candidate rows (one per lane) x 16 warps x 4 * rows
+candidate columns per lane: rows = 1 gives 64 columns (4 candidates per
+lane), rows = 2 gives 128 (8 per lane: fewer loads per evaluation, but
 batches twice as large, so fewer of them to spread over a team's CTAs).
 Which is faster depends on how many pixels each CTA of a team works on, so
 the table is keyed by radius and pixels per CTA, and measured in the batched
