@@ -368,6 +368,7 @@ struct EngSmemTail {
   int red32[32];
   unsigned long long key;  // best key of the round (leader)
   int flag;
+  int allow;  // leader: no iteration limit, status or error stops the loop after this iteration
   int stop;
   int px, py;
   uint8_t known[2][17 * 17];  // known flags of the last two targets (by round parity)
@@ -606,6 +607,9 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     // mode spread the search over more warps
     resident = m >= kEngWarps / 2 && m <= ncu && need <= avail;
   }
+  // large images: the leader publishes the next target as soon as the
+  // window's priorities are known and updates its tile maxima afterwards
+  const bool early_sel = resident && !lead_searches;
   ResPlan& pl = tl.plan;
   if (resident && searcher) {
     if (tid == 0) res_plan<R>(pl, ncu, nbands, rank, ns);
@@ -780,7 +784,8 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       status = __ldcg(&c->status);
       err = __ldcg(ea.err);
     }
-    spec_phase<R>(s, usm, uca, staged);
+    spec_phase<R>(s, usm, uca, staged, early_sel);
+    if (tid == 0) tl.allow = usm.spec_iter + 1 < lim && status == 0 && err == 0;
     if (searches) {
       const unsigned long long best = search_round(px, py);
       if (tid == 0) st_release64(&tpart[rank], key_tag(best, epoch));
@@ -789,10 +794,17 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     bool stop = true, ok = false;
     int npx = 0, npy = 0;
     unsigned long long t_b = 0ull;
+    EarlySel es{early_sel ? &tc->pub : nullptr, epoch, tl.allow != 0, ea.tick_ns, x.t_start, &tc->expired,
+                kPubThread, false};
     if (tl.flag) {
       t_b = globaltimer();
-      ok = update_phase<R>(s, nullptr, 0, usm, uca, kPubThread, false, &tl.key);  // ends with a __syncthreads
-      if (ok) {
+      ok = update_phase<R>(s, nullptr, 0, usm, uca, kPubThread, false, &tl.key, &es);  // ends with a __syncthreads
+      if (ok && es.published) {
+        // the next round (or the stop) went out inside the update phase
+        if (tid == 0) tl.stop = usm.early_stop;
+        npx = usm.next_idx % s.W;
+        npy = usm.next_idx / s.W;
+      } else if (ok) {
         // the next target is known: publish it before the bookkeeping.
         // Thread 0 decides (the inputs are global and may change under
         // other threads' feet) and the barrier below shares the decision.
@@ -814,7 +826,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     // publication: the update phase's fence (same thread) already ordered
     // every write the searchers read before this store; without an update
     // (timeout or error) the store carries its own release
-    if (tid == kPubThread) {
+    if (tid == kPubThread && !(ok && es.published)) {
       if (ok)
         st_relaxed64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
       else

@@ -22,6 +22,7 @@
 // here, which gives the same bits as evaluating the expression.
 #pragma once
 #include "inpaint_internal.cuh"
+#include "ptx.cuh"
 
 namespace inp {
 
@@ -84,6 +85,12 @@ struct __align__(16) UpdSmem {
   uint32_t ssd;
   int px, py;
   double pp, cp;
+  // the best front pixel whose priority this iteration's fill cannot change
+  // (outside the NW x NW window), found by spec_phase when asked
+  unsigned long long out_key;
+  int out_idx;
+  int early_stop;  // early selection: the loop stops after this iteration
+  PrioBest red_pb[32];
 };
 
 // Sobel normal of the Omega indicator at local (lx, ly) = image (x, y),
@@ -425,8 +432,48 @@ __device__ void stage_next(const ImgState& s, int npx, int npy, UpdSmem<R>& sm) 
 // stays in shared memory for update_phase.  Whole block.
 // `staged`: the neighbourhood of p^ is already in shared memory (the engine
 // stages it while it records the previous iteration).
+// Best (key, idx) of the priorities outside the NW x NW window around
+// (px, py), from the caches update_prefetch filled: level-1 tiles the window
+// does not touch, level-0 tiles it does not touch inside the level-1 tiles
+// it does, and the pixels outside it inside the level-0 tiles it touches.
+// Those priorities are the ones the fill of this iteration leaves alone.
+// Whole block.
 template <int R>
-__device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, bool staged) {
+__device__ void best_outside_window(const ImgState& s, UpdSmem<R>& sm, const UpdCache<R>& ca, int px,
+                                    int py) {
+  constexpr int R2 = UpdGeom<R>::R2;
+  const int W = s.W;
+  unsigned long long k = 0ull;
+  int idx = 0x7fffffff;
+  const int n1 = s.t1x * s.t1y;
+  for (int e = threadIdx.x; e < n1; e += blockDim.x) {
+    const int ux = e % s.t1x, uy = e / s.t1x;
+    if (ux >= ca.ux0 && ux < ca.ux0 + ca.nux && uy >= ca.uy0 && uy < ca.uy0 + ca.nuy) continue;
+    if (ca.t1n) prio_take(k, idx, ca.t1c[e].key, ca.t1c[e].idx);
+    else prio_take(k, idx, __ldcg(&s.tiles1[e].key), __ldcg(&s.tiles1[e].idx));
+  }
+  for (int e = threadIdx.x; e < ca.nux * ca.nuy * kT1 * kT1; e += blockDim.x) {
+    const int u = e / (kT1 * kT1), j = e % (kT1 * kT1);
+    const int tx = (ca.ux0 + u % ca.nux) * kT1 + (j & (kT1 - 1)), ty = (ca.uy0 + u / ca.nux) * kT1 + j / kT1;
+    if (tx >= ca.tx0 && tx < ca.tx0 + ca.ntx && ty >= ca.ty0 && ty < ca.ty0 + ca.nty) continue;
+    prio_take(k, idx, ca.t0c[e].key, ca.t0c[e].idx);
+  }
+  for (int e = threadIdx.x; e < ca.ntx * ca.nty * kT0 * kT0; e += blockDim.x) {
+    const int t = e / (kT0 * kT0), j = e % (kT0 * kT0);
+    const int x = (ca.tx0 + t % ca.ntx) * kT0 + (j & (kT0 - 1)), y = (ca.ty0 + t / ca.ntx) * kT0 + j / kT0;
+    if (x >= W || y >= s.H || (abs(x - px) <= R2 && abs(y - py) <= R2)) continue;
+    prio_take(k, idx, ca.tp[e], y * W + x);
+  }
+  block_best_prio(k, idx, sm.red_pb);  // ends with a __syncthreads
+  if (threadIdx.x == 0) {
+    sm.out_key = k;
+    sm.out_idx = idx;
+  }
+}
+
+template <int R>
+__device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, bool staged,
+                           bool want_outside = false) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW;
   const Ctrl* c = s.ctrl;
@@ -496,6 +543,30 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
     sm.spec_filled = filled;
   }
   __syncthreads();
+  if (want_outside) {
+    best_outside_window<R>(s, sm, ca, px, py);
+    __syncthreads();
+  }
+}
+
+// Early selection (persistent engine, resident mode): the next target is
+// the better of the best new priority in the window and the best one
+// outside it (found by spec_phase), so it is published as soon as the
+// window's priorities are known; the tile maxima are brought up to date
+// after the publication, off the searchers' path.
+struct EarlySel {
+  unsigned long long* pub;  // the team's publication word; nullptr: select through the tiles first
+  unsigned epoch;           // epoch of the round being applied
+  bool allow;               // no iteration limit, status or error stops the loop after this one
+  unsigned long long tick_ns, t_start;  // the launch's time budget (0: none) and start
+  unsigned* expired;        // set when the time budget stops the loop
+  int pub_thread;
+  bool published;           // out (every thread): the next round (or the stop) went out
+};
+
+__device__ inline unsigned long long pub_word(unsigned epoch, int px, int py, bool stop) {
+  return (unsigned long long)epoch | ((unsigned long long)(px & 0x7fff) << 32) |
+         ((unsigned long long)(py & 0x7fff) << 47) | ((unsigned long long)(stop ? 1 : 0) << 62);
 }
 
 // Update phase: applies the iteration whose best source key is *best_in, or
@@ -509,7 +580,8 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
 template <int R>
 __device__ bool update_phase(const ImgState& s, const unsigned long long* partial, int n_partial,
                              UpdSmem<R>& sm, UpdCache<R>& ca, int fence_thread = -1,
-                             bool overlap_counts = false, const unsigned long long* best_in = nullptr) {
+                             bool overlap_counts = false, const unsigned long long* best_in = nullptr,
+                             EarlySel* es = nullptr) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW, NC = G::NC;
   Ctrl* c = s.ctrl;
@@ -605,6 +677,8 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   };
   int newly = 0;
   const int nlist = (nfront + 127) & ~127;
+  unsigned long long wk = 0ull;  // best new key of the window (early selection)
+  int wi = 0x7fffffff;
   for (int t = tid; t < nlist + NW * NW + NC * NC; t += nt) {
     if (t < nlist) {
       const int k = list_entry(t);
@@ -634,6 +708,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       s.prio[p] = key;
       s.pconf[p] = cc;
       cache_prio(x, y, key);
+      prio_take(wk, wi, key, (int)p);
     } else if (t < nlist + NW * NW) {
       const int i = t - nlist;
       if (sm.snrm[i] != kSpecNotFront) continue;  // outside, or a front pixel
@@ -664,6 +739,26 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   // issued: the publishing thread fences them now, while the tiles are
   // computed, so that its publication later needs no wait of its own
   if ((int)threadIdx.x == fence_thread) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  const bool early = es && es->pub;
+  if (early) {
+    // the next target: the better of the window's best and the best outside
+    // it; published now (after the fence above, same thread) unless the loop
+    // stops, in which case the stop goes out
+    block_best_prio(wk, wi, sm.red_pb);  // every thread gets the window's best
+    prio_take(wk, wi, sm.out_key, sm.out_idx);
+    if ((int)threadIdx.x == es->pub_thread) {
+      bool st = remaining - filled <= 0 || wk == 0ull || !es->allow;
+      if (!st && es->tick_ns && globaltimer() - es->t_start > es->tick_ns) {
+        st = true;  // the launch's time budget is spent: resume in the next launch
+        *es->expired = 1u;
+      }
+      asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(es->pub),
+                   "l"(pub_word(es->epoch + 1u, st ? 0 : wi % W, st ? 0 : wi / W, st))
+                   : "memory");
+      sm.early_stop = st;
+    }
+    es->published = true;
+  }
 
   // level-0 tiles from the cached keys, then level-1, then the best
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -724,6 +819,8 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
         warp_global_best(s, k, idx);
       }
     }
+    if (early && remaining > 0 && (k != wk || (k != 0ull && idx != wi)) && tid == 0)
+      c->status = INPAINT_ERR_INTERNAL;  // the tiles and the early selection disagree
     if (tid == 0) {
       sm.next_key = k;
       sm.next_idx = idx;
