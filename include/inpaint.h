@@ -55,7 +55,14 @@ typedef enum {
 /* Search forms (both give identical results). */
 #define INPAINT_FORM_PLAIN 0 /* CUDA-core integer SSD (byte-SIMD abs-diff + dot) */
 #define INPAINT_FORM_TC 1    /* exact tensor-core correlation form (tcgen05, BF16 operands
-                                holding small integers, FP32 accumulation exact below 2^24) */
+                                holding small integers, FP32 accumulation exact below 2^24);
+                                patch_radius <= 8.  In the persistent engine (single image,
+                                teams of two or more CTAs) the image's candidates are cut
+                                into tiles of 16 rows x 512 or 1024 columns searched from
+                                five BF16 planes of the image (about 10 bytes per pixel of
+                                extra device memory); where those tiles do not fit a CTA
+                                the engine searches with the plain form.  inpaint_step
+                                always runs the graph-loop kernels. */
 
 /* Device allocator hooks: lets a host framework (e.g. PyTorch's caching
  * allocator) own device memory.  Both NULL: cudaMallocAsync/cudaFreeAsync on
@@ -141,8 +148,8 @@ void inpaint_options_default(inpaint_options* opt);
  *   patch_radius r: 1..32 (patch side P = 2r+1); W, H >= P.
  *   opt: NULL for defaults.  *out receives the context.
  * Errors: INPAINT_ERR_ARG (bad sizes/pointers, mask covering every pixel),
- * INPAINT_ERR_NOMEM, INPAINT_ERR_CUDA, INPAINT_ERR_UNSUPPORTED (TC form on
- * a device without tcgen05). On error *out is NULL and nothing leaks. */
+ * INPAINT_ERR_NOMEM, INPAINT_ERR_CUDA, INPAINT_ERR_UNSUPPORTED (TC form with
+ * patch_radius > 8). On error *out is NULL and nothing leaks. */
 int inpaint_create(const uint8_t* rgb, int width, int height, int rgb_stride_bytes,
                    const uint8_t* mask, int mask_stride_bytes, int patch_radius,
                    const inpaint_options* opt, inpaint_ctx** out);
@@ -232,6 +239,11 @@ int inpaint_info(const inpaint_ctx* ctx, int* width, int* height, int* patch_rad
  * iterations timed.  The graph loop is not timed (all zero). */
 int inpaint_loop_timing(const inpaint_ctx* ctx, uint64_t* search_ns, uint64_t* update_ns,
                         int* iters);
+
+/* Iterations since the last create/reset whose search the persistent engine
+ * ran in the tensor-core form (INPAINT_FORM_TC; the others, if any, ran the
+ * plain form, with identical results). */
+int inpaint_search_form_rounds(const inpaint_ctx* ctx, int* tc_rounds);
 
 /* Candidate-centre rectangle [x0,x1] x [y0,y1] the context searches. */
 int inpaint_search_rect(const inpaint_ctx* ctx, int* x0, int* x1, int* y0, int* y1);

@@ -192,6 +192,7 @@ SIGNATURES = {
     "inpaint_server_destroy": (None, [_P]),
     "inpaint_loop_timing": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(_I)]),
+    "inpaint_search_form_rounds": (_I, [_P, ctypes.POINTER(_I)]),
 }
 
 

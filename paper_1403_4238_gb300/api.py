@@ -195,6 +195,12 @@ class Inpainter:
                "inpaint_loop_timing")
         return a.value, b.value, n.value
 
+    def tc_rounds(self):
+        """Iterations since create/reset whose engine search ran in the tensor-core form."""
+        n = ctypes.c_int()
+        _check(self.lib.inpaint_search_form_rounds(self.ctx, ctypes.byref(n)), "inpaint_search_form_rounds")
+        return n.value
+
     def time_search(self, form: str = "plain", reps: int = 20):
         """Isolated timing of one search of `form` for the current target:
         (ms per search, best key (SSD << 32 | idx), evaluations)."""

@@ -1,6 +1,6 @@
-// Dispatch of the persistent engine by patch radius, and the TMA descriptor
-// of an image (the kernels themselves are in engine_impl.cuh, instantiated
-// per radius in engine_r<R>.cu).
+// Dispatch of the persistent engine by patch radius, the TMA descriptor of
+// an image and the planes of its tensor-core form (the kernels themselves
+// are in engine_impl.cuh, instantiated per radius in engine_r<R>.cu).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -31,6 +31,28 @@ cudaError_t launch_update_fast(const ImgState& s, unsigned long long cond, int u
 cudaError_t launch_prio_init_fast(const ImgState& s, cudaStream_t st) {
   const EngineFns* f = engine_fns(s.r);
   return f ? f->prio_init(s, st) : cudaErrorInvalidValue;
+}
+
+// The five BF16 planes of the image's current pixels (zero outside the
+// image) in the tiled layout; one thread per (tile column, row, column).
+__global__ void k_planes(ImgState s) {
+  const size_t n = (size_t)s.tc_ntx * s.prows * s.tc_len;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int xl = (int)(e % s.tc_len);
+    const size_t ry = e / s.tc_len;
+    const int y = (int)(ry % s.prows), tx = (int)(ry / s.prows);
+    const int x = s.tc_xs0 + tx * s.tc_w + xl;
+    const uint32_t w = (x < s.W && y < s.H) ? __ldg(&s.img[(size_t)y * s.pitch + x]) : 0x00808080u;
+    plane_store_at(s, tx, y, xl, w);  // outside the image: 128 - 128 = 0 everywhere
+  }
+}
+
+cudaError_t launch_planes(const ImgState& s, cudaStream_t st) {
+  if (!s.planes) return cudaSuccess;
+  const size_t n = (size_t)s.tc_ntx * s.prows * s.tc_len;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_planes<<<blocks, 256, 0, st>>>(s);
+  return cudaGetLastError();
 }
 
 // TMA descriptor of a 2-D array of 32-bit words (W x H, row pitch `pitch`

@@ -18,11 +18,13 @@
 //   3. the others wait for that epoch (bounded wait, no trap) and go on.
 // No host round trip and no kernel boundary per iteration.
 #pragma once
+#include <cstddef>
 #include <type_traits>
 #include <cuda.h>
 
 #include "inpaint_engine.h"
 #include "ptx.cuh"
+#include "search_tc_engine.cuh"
 #include "ssd_rows.cuh"
 #include "update_fast.cuh"
 
@@ -362,7 +364,7 @@ __host__ __device__ inline long long res_plan(ResPlan& pl, int ncu, int nbands, 
 // ---------------------------------------------------------------- kernel
 
 struct EngSmemTail {
-  uint64_t full[2];  // TMA completion barriers of the two streaming stages
+  EngBars bars;      // mbarriers (streaming stages, tensor-core ring), tensor-memory base
   ImgState img;      // the image's state block (a leader that does not search reads it here)
   unsigned long long red64[32];
   int red32[32];
@@ -371,9 +373,13 @@ struct EngSmemTail {
   int allow;  // leader: no iteration limit, status or error stops the loop after this iteration
   int stop;
   int px, py;
+  int a2;     // tensor-core search: sum of the known target pixels' squared shifted values
+  int tc_pref;  // tensor-core search: slots the producer prefetched for the next round
   uint8_t known[2][17 * 17];  // known flags of the last two targets (by round parity)
   ResPlan plan;               // resident mode: this CTA's units and tiles
 };
+
+static_assert(offsetof(EngSmemTail, bars) == 0, "the kernel initialises the barriers at the start of shared memory");
 
 constexpr int kTgtWords = 17 * 20 + 17 + 3;  // padded target rows + row masks (R <= 8)
 constexpr size_t kHeadBytes = ((((sizeof(EngSmemTail) + 15) & ~size_t(15)) + kTgtWords * 4 + 127) / 128) * 128;
@@ -520,6 +526,180 @@ __device__ inline bool ctrl_active(const Ctrl* c) {
 template <int R, int SRW, bool kLeadOnly = false>
 __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x);
 
+// The loop of a searching CTA in the tensor-core form (the image's state
+// block, the stop flag and the first target are in shared memory), compiled
+// as a function of its own with every phase inlined: a call would save and
+// restore the caller's registers through local memory, which misses L1
+// while shared memory takes nearly all of it.
+template <int R>
+__device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, const TcTiles tt, TcArea tca, int ns) {
+  using GT = TcEngGeom<R>;
+  constexpr int P = GT::P, NSL = GT::NSL, TP = (P + 3) & ~3;
+  uint8_t* smem = x.smem;
+  EngSmemTail& tl = *reinterpret_cast<EngSmemTail*>(smem);
+  uint32_t* tgt = reinterpret_cast<uint32_t*>(smem + ((sizeof(EngSmemTail) + 15) & ~size_t(15)));
+  const ImgState& s = tl.img;
+  Ctrl* c = s.ctrl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rank = x.rank;
+  TeamCtl* tc = x.tc;
+  const unsigned long long limit = ea.wait_limit_ns;
+  unsigned epoch = x.epoch;
+  // A | padded target | ring | validity bits
+  uint8_t* area = smem + kHeadBytes;
+  tca.a = area;
+  tca.tpad = reinterpret_cast<uint16_t*>(area + GT::A_BYTES);
+  tca.ring = area + GT::A_BYTES + GT::TPAD_BYTES;
+  tca.bits = reinterpret_cast<uint32_t*>(tca.ring + (size_t)tca.nb * tca.slot);
+  if (x.tc_nb != tca.nb) {
+    // the ring's phases are counted from the slot sequence number modulo the
+    // slot count: a new slot count restarts them (every slot of an earlier
+    // image was consumed, so no barrier has a pending phase)
+    if (x.tc_nb != 0 && tid == 0) {
+      for (int i = 0; i < kTcRing; ++i) {
+        mbar_inval(&tl.bars.tc_full[i]);
+        mbar_inval(&tl.bars.tc_empty[i]);
+        mbar_init(&tl.bars.tc_full[i], 1);
+        mbar_init(&tl.bars.tc_empty[i], 2);
+      }
+    }
+    fence_mbar_init();
+    __syncthreads();
+    x.tc_nb = tca.nb;
+    x.tc_rows = 0;
+  }
+  const int ntiles = tt.ntx * tt.nty;
+  const int first_y = s.cy0 + kTcRows * (rank / tt.ntx), first_tx = rank % tt.ntx;  // this CTA's first tile
+  const int npre = min(tca.nb, NSL);
+  int prev_px = -1000000, prev_py = -1000000;
+  int round = 0;
+  while (!tl.stop) {
+    const int px = tl.px, py = tl.py;
+    const int par = round & 1;
+    const bool first = round == 0;
+    int bad = 0;
+    // the producer starts the first tile's rows at once, unless it
+    // prefetched them while the leader was updating
+    if (x.tc_pref == 0 && warp == kEngWarps - 1 && lane == 0 &&
+        !tc_produce<R>(s, tca, tl.bars, first_tx, first_y, x.tc_rows, 0, npre, limit))
+      bad = 1;
+    if (first) tc_bits_init<R>(s, tt, tca.bits, tca.ntl, rank, ns);
+    // target patch: warp dy reads row dy (lane = dx)
+    uint8_t* kn = tl.known[par];
+    for (int dy = warp; dy < P; dy += kEngWarps) {
+      const int tx = px + lane - R, ty = py + dy - R;
+      uint32_t w = 0;
+      bool known = false;
+      if (lane < P && tx >= 0 && tx < s.W && ty >= 0 && ty < s.H) {
+        const uint8_t o = __ldcg(&s.omega[(size_t)ty * s.W + tx]);
+        const uint32_t v = __ldcg(&s.img[(size_t)ty * s.pitch + tx]);
+        known = o == 0;
+        w = known ? v : 0u;
+      }
+      if (lane < P) {
+        tgt[dy * TP + lane] = w;
+        kn[dy * P + lane] = (uint8_t)known;
+      }
+    }
+    __syncthreads();
+    tc_target<R>(tca.tpad, tgt, TP, kn, &tl.a2);
+    __syncthreads();
+    // every warp but the producer's (its copies are in flight) writes A
+    tc_build_a<R>(tca.a, tca.tpad, first, 32 * (kEngWarps - 1));
+    __syncthreads();
+    const int a2 = tl.a2;
+    unsigned long long best = ~0ull;
+    for (int kt = 0; kt < tca.ntl; ++kt) {
+      const int t = rank + kt * ns;
+      if (t >= ntiles) break;  // uniform
+      const int y0 = s.cy0 + kTcRows * (t / tt.ntx), xs = tt.xs0 + 8 * tt.N * (t % tt.ntx);
+      const uint32_t g0 = x.tc_rows;
+      if (warp == kEngWarps - 1) {
+        if (lane == 0 && !tc_produce<R>(s, tca, tl.bars, t % tt.ntx, y0, g0, kt == 0 ? npre : 0, NSL, limit))
+          bad = 1;
+        __syncwarp();
+      } else if (warp == kEngWarps - 2) {
+        if (!(tt.N == 128 ? tc_issue<R, 0, 128>(tca, tl.bars, x.tmem, g0, limit)
+                          : tc_issue<R, 0, 64>(tca, tl.bars, x.tmem, g0, limit)))
+          bad = 1;
+        // the one warp that waits for the tile's MMAs (the others sleep at
+        // the block barrier: spinning warps would take issue slots from the
+        // issuers)
+        if (!mbar_wait(&tl.bars.tc_done, x.tc_tiles & 1u, limit)) bad = 1;
+      } else if (warp == kEngWarps - 3) {
+        if (!(tt.N == 128 ? tc_issue<R, 1, 128>(tca, tl.bars, x.tmem, g0, limit)
+                          : tc_issue<R, 1, 64>(tca, tl.bars, x.tmem, g0, limit)))
+          bad = 1;
+      } else if (kt == 0 && !first) {
+        // validity bits near the previous fill: needed only by the read-back
+        tc_bits_refresh<R>(s, tt, tca.bits, rank, ns, prev_px, prev_py, 32 * (kEngWarps - 3));
+      }
+      tc_fence_before();
+      if (__syncthreads_or(bad)) break;
+      tc_fence_after();
+      best = tc_epilogue<R>(s, x.tmem, tt.N, a2, tca.bits + kt * tc_bit_words(tt.N), y0, xs, best);
+      tc_fence_before();
+      ++x.tc_tiles;
+      x.tc_rows += NSL;
+      __syncthreads();  // the accumulators are read before the next tile's MMAs
+    }
+    x.tc_pref = 0;
+    best = block_min_u64(best, tl.red64);
+    ++round;
+    if (bad && tid == 0) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
+    if (tid == 0 && rank + 1 != ea.withhold) st_release64(&x.tpart[rank], key_tag(best, epoch));
+    if (rank == 0 && tid == 0) atomicAdd(&c->tc_rounds, 1);
+    if (warp == kEngWarps - 1 && lane == 0) {
+      // once the leader has written this round's fill, the next round's
+      // first source rows are final: request them now, while the leader
+      // updates (no prefetch if the next publication comes first)
+      int n = 0;
+      const unsigned long long t0 = globaltimer();
+      while (true) {
+        if ((int)(ld_acquire(&tc->copied) - (epoch + 1u)) >= 0) {
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          n = npre;
+          if (!tc_produce<R>(s, tca, tl.bars, first_tx, first_y, x.tc_rows, 0, n, limit))
+            atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
+          break;
+        }
+        if ((unsigned)ld_acquire64(&tc->pub) != epoch || globaltimer() - t0 > limit) break;
+      }
+      tl.tc_pref = n;
+    }
+    // wait for the next round
+    if (tid == 0) {
+      const unsigned long long v = wait_pub(tc, epoch, ea.err, limit);
+      tl.stop = ((v >> 62) & 1ull) != 0;
+      tl.px = (int)((v >> 32) & 0x7fff);
+      tl.py = (int)((v >> 47) & 0x7fff);
+    }
+    ++epoch;
+    prev_px = px;
+    prev_py = py;
+    __syncthreads();
+    x.tc_pref = tl.tc_pref;
+    if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  if (x.tc_pref > 0) {
+    // the loop stopped with a prefetch in flight: let it land and release
+    // its slots (two arrivals stand for the two issuers' commits)
+    if (warp == kEngWarps - 1 && lane == 0) {
+      for (int h = 0; h < x.tc_pref; ++h) {
+        const uint32_t g = x.tc_rows + (uint32_t)h;
+        const int slot = (int)(g % (uint32_t)tca.nb);
+        if (!mbar_wait(&tl.bars.tc_full[slot], (g / tca.nb) & 1u, limit)) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
+        mbar_arrive(&tl.bars.tc_empty[slot]);
+        mbar_arrive(&tl.bars.tc_empty[slot]);
+      }
+    }
+    x.tc_rows += (uint32_t)x.tc_pref;
+    x.tc_pref = 0;
+    __syncthreads();
+  }
+  x.epoch = epoch;
+}
+
 // The loop of a leader that does not search, compiled as a function of its
 // own: none of the search state is live through its phases, so its
 // registers hold the update's working set.
@@ -570,13 +750,45 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   // searches its share after the speculative phase, which is short next to
   // a CTA's share of such a search.  A CTA that neither searches nor leads
   // idles until the image is done.
-  const bool lead_searches = tsize == 1 || nbatch >= 8 * tsize;
-  const int ns = lead_searches ? tsize : min(tsize - 1, nbatch);
+  // Tensor-core form (an image given planes, a team of two or more): every
+  // CTA but the leader searches whole tiles, when its A strips, a ring of
+  // at least four source-row slots and the validity bits of its tiles fit.
+  const TcTiles tt = s.planes ? tc_tiles(s) : TcTiles{0, 0, 0, 0};
+  const int tc_ntiles = tt.ntx * tt.nty;
+  TcArea tca{nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
+  bool tcmode = false;
+  if (s.planes && ea.tc_cols >= 2 * tt.N && tsize >= 2 && tc_ntiles > 0) {
+    const int nsq = min(tsize - 1, tc_ntiles);
+    const int ntl = (tc_ntiles + nsq - 1) / nsq;
+    const long long avail = (long long)(x.smem_end - (smem + kHeadBytes));
+    const int slot = tc_slot(tt.N, R);
+    const long long fixed =
+        TcEngGeom<R>::A_BYTES + TcEngGeom<R>::TPAD_BYTES + (long long)ntl * tc_bit_words(tt.N) * 4;
+    const long long nbl = (avail - fixed) / slot;
+    if (ntl <= 8 && nbl >= 4) {
+      tcmode = true;
+      tca.nb = nbl < kTcRing ? (int)nbl : kTcRing;
+      tca.ntl = ntl;
+      tca.slot = slot;
+    }
+  }
+  const bool lead_searches = !tcmode && (tsize == 1 || nbatch >= 8 * tsize);
+  const int ns = tcmode ? min(tsize - 1, tc_ntiles) : lead_searches ? tsize : min(tsize - 1, nbatch);
   const bool leader = rank == tsize - 1;
   const bool searcher = rank < ns;
   if constexpr (!kLeadOnly) {
     if (leader && !searcher) {
       run_lead_only<R, SRW>(ea, j, x);
+      return;
+    }
+    if (tcmode && searcher) {
+      if (tid == 0) {
+        tl.stop = !ctrl_active(c) || __ldcg(ea.err) != 0;
+        tl.px = __ldcg(&c->px);
+        tl.py = __ldcg(&c->py);
+      }
+      __syncthreads();
+      run_tc_search<R>(ea, x, tt, tca, ns);
       return;
     }
   }
@@ -605,11 +817,11 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
                                (m * kResCols + 2 * (2 * R + 8)) + 256 + m * 64;
     // at least half a unit per warp, else the batches of the streaming
     // mode spread the search over more warps
-    resident = m >= kEngWarps / 2 && m <= ncu && need <= avail;
+    resident = !tcmode && m >= kEngWarps / 2 && m <= ncu && need <= avail;
   }
   // large images: the leader publishes the next target as soon as the
   // window's priorities are known and updates its tile maxima afterwards
-  const bool early_sel = resident && !lead_searches;
+  const bool early_sel = (resident || tcmode) && !lead_searches;
   ResPlan& pl = tl.plan;
   if (resident && searcher) {
     if (tid == 0) res_plan<R>(pl, ncu, nbands, rank, ns);
@@ -641,7 +853,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       tma_load_2d(ct, cmap, xb - G::COFF + G::BWC * gx, s.cy0 + B * gy, bar);
     };
     const bool first = round == 0;
-    if (!resident && tid == 0 && b0 < nbatch) issue(b0, slot_pix(0), cnt_t[0], &tl.full[0]);
+    if (!resident && tid == 0 && b0 < nbatch) issue(b0, slot_pix(0), cnt_t[0], &tl.bars.full[0]);
     const uint8_t* tiles = area;
     if (resident && first) {
       // the source windows of every band segment (plain 16-byte loads;
@@ -736,9 +948,9 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       int cur = 0;
       for (int b = b0; b < nbatch; b += ns) {
         const int nb = b + ns;
-        if (tid == 0 && nb < nbatch) issue(nb, slot_pix(cur ^ 1), cnt_t[cur ^ 1], &tl.full[cur ^ 1]);
+        if (tid == 0 && nb < nbatch) issue(nb, slot_pix(cur ^ 1), cnt_t[cur ^ 1], &tl.bars.full[cur ^ 1]);
         const int gx = b % ncg, gy = b / ncg;
-        const bool got = mbar_wait(&tl.full[cur], cur ? ph1 : ph0, limit);
+        const bool got = mbar_wait(&tl.bars.full[cur], cur ? ph1 : ph0, limit);
         if (cur) ph1 ^= 1; else ph0 ^= 1;
         // validity of this lane's candidates from the count tile (16-byte
         // aligned chunk) and the search rectangle
@@ -757,7 +969,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
         if (__syncthreads_or(!got)) {  // a bounded wait gave up: stop uniformly
           ok = false;
           if (nb < nbatch) {
-            mbar_wait(&tl.full[cur ^ 1], cur ? ph0 : ph1, limit);
+            mbar_wait(&tl.bars.full[cur ^ 1], cur ? ph0 : ph1, limit);
             if (cur) ph0 ^= 1; else ph1 ^= 1;
           }
           break;
@@ -798,7 +1010,8 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
                 kPubThread, false};
     if (tl.flag) {
       t_b = globaltimer();
-      ok = update_phase<R>(s, nullptr, 0, usm, uca, kPubThread, false, &tl.key, &es);  // ends with a __syncthreads
+      ok = update_phase<R>(s, nullptr, 0, usm, uca, kPubThread, false, &tl.key, &es,
+                           tcmode ? &tc->copied : nullptr, epoch + 1u);  // ends with a __syncthreads
       if (ok && es.published) {
         // the next round (or the stop) went out inside the update phase
         if (tid == 0) tl.stop = usm.early_stop;

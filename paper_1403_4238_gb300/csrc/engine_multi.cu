@@ -3,6 +3,7 @@
 // CTAs; batch: many teams, each with a list of images).  The per-image body
 // for the image's patch radius is selected at run time.
 #include "inpaint_engine.h"
+#include "ptx.cuh"
 
 namespace inp {
 
@@ -42,14 +43,31 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
   x.tsize = ea.team_first[team + 1] - first;
   x.tc = &ea.teams[team];
   x.tpart = ea.partials + first;
-  // the two TMA completion barriers sit at the start of shared memory
-  uint64_t* bars = reinterpret_cast<uint64_t*>(x.smem);
+  // the barriers sit at the start of shared memory
+  EngBars* bars = reinterpret_cast<EngBars*>(x.smem);
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bars[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bars[1])) : "memory");
+    mbar_init(&bars->full[0], 1);
+    mbar_init(&bars->full[1], 1);
+    if (ea.tc_cols > 0) {
+      for (int i = 0; i < kTcRing; ++i) {
+        mbar_init(&bars->tc_full[i], 1);
+        mbar_init(&bars->tc_empty[i], 2);  // one commit from each issuer
+      }
+      mbar_init(&bars->tc_done, 2);
+    }
   }
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  fence_mbar_init();
+  // tensor memory of the tensor-core search: held for the whole launch (one
+  // CTA per SM, so the allocation never waits on another engine CTA)
+  if (ea.tc_cols > 0 && threadIdx.x < 32) tc_alloc(&bars->tmem, (uint32_t)ea.tc_cols);
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  x.tmem = ea.tc_cols > 0 ? bars->tmem : 0u;
+  x.tc_rows = 0;
+  x.tc_tiles = 0;
+  x.tc_nb = 0;
+  x.tc_pref = 0;
   x.ph0 = 0;
   x.ph1 = 0;
   x.epoch = (unsigned)ld_acquire64_pub(&x.tc->pub);
@@ -61,6 +79,15 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(EngineArgs ea) {
     unsigned expired;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(expired) : "l"(&x.tc->expired) : "memory");
     if (expired) break;
+  }
+  // every tile's MMAs were waited for before its accumulators were read
+  if (ea.tc_cols > 0) {
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      tc_fence_after();
+      tc_dealloc(x.tmem, (uint32_t)ea.tc_cols);
+    }
   }
 }
 

@@ -192,9 +192,7 @@ int launch_iteration(inpaint_ctx* c, int use_cond) {
 }
 
 bool use_engine(const inpaint_ctx* c) {
-  if (c->opt.loop_mode == INPAINT_LOOP_GRAPH || c->opt.form == INPAINT_FORM_TC ||
-      c->opt.search_variant != INPAINT_SEARCH_FULL)
-    return false;
+  if (c->opt.loop_mode == INPAINT_LOOP_GRAPH || c->opt.search_variant != INPAINT_SEARCH_FULL) return false;
   return c->r <= 8;
 }
 
@@ -289,6 +287,7 @@ int setup_engine(inpaint_ctx* c) {
   ea.partials = c->d_epart;
   ea.err = c->d_err;
   ea.wait_limit_ns = 4000000000ull;  // 4 s: far beyond any iteration
+  ea.tc_cols = c->st.planes ? 256 : 0;  // X and S accumulators of N <= 128 columns each
   c->eng_ready = true;
   return INPAINT_OK;
 }
@@ -298,6 +297,7 @@ int run_engine(inpaint_ctx* c) {
   if (rc) return rc;
   CK(cudaMemsetAsync(c->d_team, 0, sizeof(TeamCtl), c->stream));
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CK(launch_planes(c->st, c->stream));  // the image may have changed since the last launch
   CK(engine_launch(c->eng_smem, c->ea, c->eng_grid, c->stream));
   CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   return INPAINT_OK;
@@ -364,8 +364,8 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
     g_last_error = "dev_alloc and dev_free must be given together";
     return INPAINT_ERR_ARG;
   }
-  if (o.form == INPAINT_FORM_TC && (r > 8 || o.loop_mode == INPAINT_LOOP_ENGINE)) {
-    g_last_error = "the tensor-core form supports patch_radius <= 8 in the graph loop";
+  if (o.form == INPAINT_FORM_TC && r > 8) {
+    g_last_error = "the tensor-core form supports patch_radius <= 8";
     return INPAINT_ERR_UNSUPPORTED;
   }
   if (o.search_variant != INPAINT_SEARCH_FULL && o.search_variant != INPAINT_SEARCH_OVERLAP)
@@ -433,6 +433,14 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
       !alloc_n(c, c->mask_stage, n)) {
     g_last_error = "device allocation failed";
     return fail(INPAINT_ERR_NOMEM);
+  }
+  if (o.form == INPAINT_FORM_TC && o.loop_mode != INPAINT_LOOP_GRAPH) {
+    // the engine's tensor-core search reads five BF16 planes of the image
+    const size_t np = tc_plane_layout(s);
+    if (np > 0 && !alloc_n(c, s.planes, np)) {
+      g_last_error = "device allocation failed";
+      return fail(INPAINT_ERR_NOMEM);
+    }
   }
   if (prepare_search_plain(r) != cudaSuccess) return fail(INPAINT_ERR_CUDA);
   if (o.form == INPAINT_FORM_TC && encode_search_tc(s, &c->tc) != cudaSuccess) {
@@ -799,6 +807,14 @@ int inpaint_loop_timing(const inpaint_ctx* c, uint64_t* search_ns, uint64_t* upd
   if (search_ns) *search_ns = c->h_ctrl->t_search;
   if (update_ns) *update_ns = c->h_ctrl->t_update;
   if (iters) *iters = c->h_ctrl->timed_iters;
+  return INPAINT_OK;
+}
+
+int inpaint_search_form_rounds(const inpaint_ctx* c, int* tc_rounds) {
+  if (!c || !tc_rounds) return INPAINT_ERR_ARG;
+  int rc = read_ctrl(c);
+  if (rc) return rc;
+  *tc_rounds = c->h_ctrl->tc_rounds;
   return INPAINT_OK;
 }
 

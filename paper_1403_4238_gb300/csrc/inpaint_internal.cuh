@@ -20,10 +20,14 @@
 //                        argmax over the front reads only these few entries
 //   ctrl   Ctrl          loop control block (selected p^, counters, status)
 //   trace  inpaint_step_info[trace_cap]   one record per iteration
+//   planes uint16[5][prows*ppitch]  tensor-core form in the engine only: BF16
+//                        R' G' B' (byte - 128) and the two halves of the
+//                        square sum, the operands of its correlations
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "inpaint.h"
 
@@ -70,7 +74,7 @@ struct Ctrl {
   // previous publish to the last arrival) and update phase, summed
   unsigned long long t_search, t_update, t_last;
   int timed_iters;
-  int pad1;
+  int tc_rounds;   // engine search rounds run in the tensor-core form
 };
 
 // Window codes of the speculative phase (update_fast.cuh): a pixel of the
@@ -131,7 +135,47 @@ struct ImgState {
   inpaint_step_info* trace;
   unsigned long long* partial;  // per-CTA best search key of the iteration
   const double* dtab;           // data-term table (device, shared by contexts)
+  // tensor-core form in the persistent engine (null otherwise): five BF16
+  // planes of the image, R' G' B' (byte - 128) and the square sum
+  // sq = sum_c (byte_c - 128)^2 as 256 hi and lo (sq = 256 hi + lo), stored per tile column tx
+  // of the search (columns [tc_xs0 + tx * tc_w, + tc_len)) as
+  // [tx][row y < prows][plane][tc_len], zero outside W x H, so that two
+  // source rows of a tile are one contiguous copy
+  uint16_t* planes;
+  int prows, tc_xs0, tc_w, tc_len, tc_ntx;
 };
+
+// BF16 bits of an integer with at most 8 significant bits (|v| <= 256, or
+// 256 times such a value: exact, the low half of the float is zero).
+__host__ __device__ inline uint32_t bf16_of_int(int v) {
+  const float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return u >> 16;
+}
+
+// The five plane values of pixel word w (R' G' B' hi lo) at offset o of
+// tile column tx, row y.
+__device__ inline void plane_store_at(const ImgState& s, int tx, int y, int o, uint32_t w) {
+  const int d0 = (int)(w & 255u) - 128, d1 = (int)((w >> 8) & 255u) - 128, d2 = (int)((w >> 16) & 255u) - 128;
+  const int sq = d0 * d0 + d1 * d1 + d2 * d2;
+  uint16_t* row = s.planes + ((size_t)tx * s.prows + y) * 5 * s.tc_len + o;
+  row[0] = (uint16_t)bf16_of_int(d0);
+  row[s.tc_len] = (uint16_t)bf16_of_int(d1);
+  row[2 * s.tc_len] = (uint16_t)bf16_of_int(d2);
+  row[3 * s.tc_len] = (uint16_t)bf16_of_int(sq & ~255);  // 256 hi: hi < 256, exact in BF16
+  row[4 * s.tc_len] = (uint16_t)bf16_of_int(sq & 255);
+}
+
+// Pixel (x, y) changed to w: its copies in the (at most two) tile columns
+// whose segments hold column x.
+__device__ inline void plane_store(const ImgState& s, int x, int y, uint32_t w) {
+  const int xl = x - s.tc_xs0;
+  if (xl < 0) return;  // left of every tile's source columns
+  int tx = xl / s.tc_w;
+  if (tx >= s.tc_ntx) tx = s.tc_ntx - 1;
+  for (; tx >= 0 && xl - tx * s.tc_w < s.tc_len; --tx) plane_store_at(s, tx, y, xl - tx * s.tc_w, w);
+}
 
 __host__ __device__ inline uint32_t pack_rgb(uint32_t r, uint32_t g, uint32_t b) {
   return r | (g << 8) | (b << 16);

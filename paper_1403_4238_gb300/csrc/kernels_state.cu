@@ -123,6 +123,7 @@ __global__ void k_ctrl_init(Ctrl* c) {
   c->t_update = 0ull;
   c->t_last = 0ull;
   c->timed_iters = 0;
+  c->tc_rounds = 0;
 }
 
 // RGB (or RGBA words) + mask -> packed state; counts |Omega|.
@@ -317,6 +318,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(ImgState s, int do_fill,
         if (s.omega[t]) {
           const uint32_t w = s.img[(size_t)(qy + dy) * s.pitch + qx + dx];
           s.img[(size_t)ty * s.pitch + tx] = w;
+          if (s.planes) plane_store(s, tx, ty, w);
           s.gray[t] = (uint8_t)luma_word(w);
           s.conf[t] = cp;
           s.omega[t] = 0;

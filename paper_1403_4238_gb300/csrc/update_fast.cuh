@@ -581,7 +581,7 @@ template <int R>
 __device__ bool update_phase(const ImgState& s, const unsigned long long* partial, int n_partial,
                              UpdSmem<R>& sm, UpdCache<R>& ca, int fence_thread = -1,
                              bool overlap_counts = false, const unsigned long long* best_in = nullptr,
-                             EarlySel* es = nullptr) {
+                             EarlySel* es = nullptr, unsigned* copied = nullptr, unsigned copied_val = 0u) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW, NC = G::NC;
   Ctrl* c = s.ctrl;
@@ -631,12 +631,20 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     const uint8_t g = (uint8_t)luma_word(w);
     const size_t t = (size_t)ty * W + tx;
     s.img[(size_t)ty * s.pitch + tx] = w;
+    if (s.planes) plane_store(s, tx, ty, w);  // the tensor-core search's operands
     s.gray[t] = g;
     s.conf[t] = cp;
     s.omega[t] = 0;
     sm.gr[l] = g;
   }
   __syncthreads();
+  if (copied && tid == 0) {
+    // the fill is in the image (and its planes): the searchers may prefetch
+    // the next round's source rows (the barrier above orders every thread's
+    // copy before this release)
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(copied), "r"(copied_val) : "memory");
+  }
   const int nx_in = min(px + R, W - 1) - max(px - R, 0) + 1;
   const int ny_in = min(py + R, H - 1) - max(py - R, 0) + 1;
   const int n_known = nx_in * ny_in - filled;

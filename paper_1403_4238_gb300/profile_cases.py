@@ -9,8 +9,9 @@ filter and a launch count:
     python -m paper_1403_4238_gb300.profile_cases search_plain_1080p --reps 3
 
 engine_*   whole removals (one persistent k_engine launch each, plus the
-           initialisation kernels), plain form; --iters N stops each launch
-           after N iterations (a shorter launch for a full-counter capture);
+           initialisation kernels), plain form (engine_tc_*: the tensor-core
+           form); --iters N stops each launch after N iterations (a shorter
+           launch for a full-counter capture);
 search_*   the findBestPatch kernel of one form alone, for the first target
            of the removal (inpaint_time_search), after one untimed launch.
 """
@@ -21,8 +22,10 @@ import argparse
 from . import api, synth
 
 CASES = {
-    "engine_512x384": (synth.walkingman_like, "engine", None),
-    "engine_1080p": (synth.hd_blob, "engine", None),
+    "engine_512x384": (synth.walkingman_like, "engine", "plain"),
+    "engine_1080p": (synth.hd_blob, "engine", "plain"),
+    "engine_tc_512x384": (synth.walkingman_like, "engine", "tc"),
+    "engine_tc_1080p": (synth.hd_blob, "engine", "tc"),
     "search_tc_512x384": (synth.walkingman_like, "search", "tc"),
     "search_plain_512x384": (synth.walkingman_like, "search", "plain"),
     "search_tc_1080p": (synth.hd_blob, "search", "tc"),
@@ -36,7 +39,7 @@ def run(name: str, reps: int, iters: int = 0):
     make, kind, form = CASES[name]
     case = make()
     if kind == "engine":
-        with api.Inpainter(case.rgb, case.mask, case.r, loop="engine") as ip:
+        with api.Inpainter(case.rgb, case.mask, case.r, form=form, loop="engine") as ip:
             drgb, dmask = torch.from_numpy(case.rgb).cuda(), torch.from_numpy(case.mask).cuda()
             for _ in range(reps):
                 ip.reset(drgb, dmask)

@@ -88,14 +88,18 @@ def hd():
     return e, make_case(e), trace_rows(e)
 
 
-@pytest.mark.parametrize("form,loop", [("plain", "engine"), ("plain", "graph"), ("tc", "graph")])
+@pytest.mark.parametrize("form,loop", [("plain", "engine"), ("plain", "graph"), ("tc", "engine"),
+                                       ("tc", "graph")])
 def test_full_hd_removal_equals_oracle(api, hd, form, loop):
     e, case, rows = hd
     with api.Inpainter(case.rgb, case.mask, case.r, form=form, loop=loop) as ip:
         rc, n, tr = ip.run(trace=True)
         out = ip.result()
         info = ip.info()
+        tc_rounds = ip.tc_rounds()
     assert rc == 0 and n == e["iters"]
+    # the engine's tensor-core form searched every iteration
+    assert tc_rounds == (n if (form, loop) == ("tc", "engine") else 0)
     assert_trace_matches(tr, rows)
     assert sha(out) == e["result_sha256"]
     assert info["evals"] == e["evals"] and info["remaining"] == 0
