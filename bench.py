@@ -3,18 +3,20 @@
 Headline workload (one "step"): one whole object removal of a 1920x1080
 synthetic image with a random-walk blob mask covering about 5 % of the
 pixels, 13x13 patches (radius 6), exhaustive search -- initialisation from
-inputs already in HBM, then the device-driven fill loop (persistent engine,
-plain CUDA-core search) until the target region is empty.  The metric is
-candidate-pixel SSD evaluations per second (one evaluation = one valid
-candidate x one known target pixel, all three channels), counted exactly by
-the device loop; ms per removal is reported beside it.
+inputs already in HBM, then the device-driven fill loop (persistent engine
+with the exact tensor-core search, --form plain for the CUDA-core search)
+until the target region is empty.  The metric is candidate-pixel SSD
+evaluations per second (one evaluation = one valid candidate x one known
+target pixel, all three channels), counted exactly by the device loop; ms
+per removal is reported beside it, and the line's "plain_engine" holds the
+same removal with the plain form (time, roofline, and the speedup).
 
 Beside the headline the same JSON line carries:
   walkingman  the 512x384 removal (3 ellipses, 8 %, 9x9 patches) with the
               headline's keys (value, e2e, roofline, cpu_baseline);
-  tc          the exact tensor-core search form on both removals (whole
-              removal and the search kernel alone), as speedups over the
-              plain form, outputs compared;
+  tc, tc_hd  the exact tensor-core search form on both removals (whole
+              removal in the engine and in the graph loop, and the search
+              kernel alone), as speedups over the plain form, outputs compared;
   batched     64 images of uneven sizes in one persistent launch (CUDA
               graph), images/s and the speedup over one after another;
   serving     Poisson arrivals through the continuous-batching server under
@@ -53,7 +55,8 @@ if ROOT not in sys.path:
 METRIC = "candidate-pixel SSD evals/s (whole removal, 1920x1080, 13x13 patch, exhaustive search)"
 UNIT = "evals/s"
 WORKLOAD = ("1920x1080 RGB, random-walk blob mask 4.5% (93,336 px), r=6 (13x13), exhaustive search, "
-            "plain form, persistent engine")
+            "{form} form, persistent engine")
+FORM_NAMES = {"tc": "exact tensor-core", "plain": "plain CUDA-core"}
 WORKLOAD2 = "512x384 RGB, 3-ellipse mask 7.5-8.5%, r=4 (9x9), exhaustive search, plain form, persistent engine"
 
 
@@ -63,6 +66,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--form", default="tc", choices=["tc", "plain"],
+                    help="search form of the headline removal (the other one is timed beside it)")
     ap.add_argument("--cpu-iters", type=int, default=12,
                     help="oracle iterations of the CPU sample (a bounded prefix of the removal)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -235,8 +240,32 @@ INT32_OPS_PER_EVAL = 6
 # The committed ncu summary of the headline kernel: the DRAM bytes of one
 # launch and the digest of the kernel sources the capture was taken on.
 ENGINE_PROFILE = os.path.join(ROOT, "profiles", "k_engine_1920x1080.md")
+ENGINE_TC_PROFILE = os.path.join(ROOT, "profiles", "k_engine_tc_1920x1080.md")
 ENGINE_SOURCES = ("engine_impl.cuh", "engine_multi.cu", "update_fast.cuh", "inpaint_engine.h",
-                  "inpaint_internal.cuh", "ptx.cuh", "gen_ssd_rows.py")
+                  "inpaint_internal.cuh", "ptx.cuh", "gen_ssd_rows.py", "search_tc_engine.cuh")
+
+# Tensor-core form, algorithmic work per evaluation: the im2col INT8 count
+# of the expanded SSD, 3 weight sets x 3 channels = 9 MACs (18 FLOP); the
+# exact BF16 form of this library does 5 useful MACs (3 colour products
+# and the two halves of the squared source norm).  The MMAs it executes
+# per tile follow from its geometry (Toeplitz target rows x 16 candidate
+# rows x 8 shifts against N blocks of 8 candidate columns).
+TC_ALGO_FLOP_PER_EVAL = 18
+TC_USEFUL_FLOP_PER_EVAL = 10
+
+
+def tc_mmas_per_iteration(W, H, r):
+    """MMAs (128 x N x 16) one search of the engine's tensor-core form issues."""
+    cx0, cx1, cy0, cy1 = r, W - 1 - r, r, H - 1 - r
+    xs0 = (cx0 - r) & ~7
+    wneed = cx1 - r - xs0 + 1
+    ntx = (wneed + 1023) // 1024
+    n = 64 if (wneed + 8 * ntx - 1) // (8 * ntx) <= 64 else 128
+    nty = (cy1 - cy0 + 16) // 16
+    p = 2 * r + 1
+    nc = (p + 14) // 8
+    per_tile = (16 + p - 1) * ((3 * nc + 1) // 2 + nc)
+    return ntx * nty * per_tile, n
 
 
 def engine_source_digest() -> str:
@@ -247,10 +276,10 @@ def engine_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def engine_traffic():
+def engine_traffic(path=ENGINE_PROFILE):
     """(bytes per launch, note) from the committed capture, or (None, why)."""
     try:
-        with open(ENGINE_PROFILE) as f:
+        with open(path) as f:
             text = f.read()
     except OSError:
         return None, "no committed capture"
@@ -352,6 +381,27 @@ def roofline_plain(evals, run_ms, sms, mhz, peaks_probe, traffic):
     return out
 
 
+def roofline_tc(evals, iters, W, H, r, run_ms, peaks, traffic):
+    """Tensor-bound roofline of the engine's tensor-core form."""
+    peak = peaks.get("bf16_tflops")
+    secs = run_ms / 1e3
+    ach = evals * TC_ALGO_FLOP_PER_EVAL / secs / 1e12
+    mmas, n = tc_mmas_per_iteration(W, H, r)
+    executed = iters * mmas * 2 * 128 * n * 16 / secs / 1e12
+    useful = evals * TC_USEFUL_FLOP_PER_EVAL / secs / 1e12
+    out = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+           "frac": ach / peak if peak else None,
+           "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if peak else None,
+           "algorithmic": f"{TC_ALGO_FLOP_PER_EVAL} FLOP per evaluation (9 MACs: 3 weight sets x 3 channels)",
+           "useful_bf16": {"achieved": useful, "frac": useful / peak if peak else None,
+                           "note": "5 MACs per evaluation: 3 colour products, 2 halves of the square norm"},
+           "executed_mma": {"achieved": executed, "frac": executed / peak if peak else None,
+                            "mmas_per_iteration": mmas, "shape": f"128x{n}x16",
+                            "note": "MMA work issued, zero-padded Toeplitz rows included"}}
+    out["traffic"], out["traffic_note"] = traffic
+    return out
+
+
 def single_section(api, case, flush, steps, warmup, peaks_probe, traffic, world, cpu_iters, sms, mhz):
     """One removal timed as the headline is: device-resident inputs, L2
     flushed between steps; the same metric end to end from host buffers;
@@ -380,16 +430,20 @@ def single_section(api, case, flush, steps, warmup, peaks_probe, traffic, world,
     return res, out_img
 
 
-def tc_section(api, case, flush, steps, peaks, plain_ms, plain_out):
-    """Tensor-core form vs the plain form on one removal: whole removal and
-    the search kernel alone (first target), outputs compared."""
+def tc_section(api, case, flush, steps, peaks, known):
+    """Tensor-core form vs the plain form on one removal: whole removal in
+    the engine and in the graph loop, the search kernel alone (first
+    target), outputs compared.  known: {(form, loop): (ms, image)} already
+    timed by the caller."""
     import torch
 
     drgb = torch.from_numpy(case.rgb).cuda()
     dmask = torch.from_numpy(case.mask).cuda()
     out = {"workload": f"{case.mask.shape[1]}x{case.mask.shape[0]} r={case.r}"}
-    res = {("plain", "auto"): (plain_ms, plain_out)}
-    for form, loop in (("plain", "graph"), ("tc", "graph")):
+    res = dict(known)
+    for form, loop in (("plain", "engine"), ("tc", "engine"), ("plain", "graph"), ("tc", "graph")):
+        if (form, loop) in res:
+            continue
         with api.Inpainter(case.rgb, case.mask, case.r, form=form, loop=loop) as ip:
             ms, _, n = time_removals(ip, drgb, dmask, steps, 1, flush)
             res[(form, loop)] = (ms, ip.result())
@@ -397,29 +451,25 @@ def tc_section(api, case, flush, steps, peaks, plain_ms, plain_out):
     with api.Inpainter(case.rgb, case.mask, case.r, loop="graph") as ip:
         s_plain, k_plain, ev = ip.time_search("plain", 20)
         s_tc, k_tc, _ = ip.time_search("tc", 20)
-    base_ms, base_img = res[("plain", "auto")]
+    base_ms, base_img = res[("plain", "engine")]
     out.update({
-        "ms_per_removal": {"plain_engine": base_ms, "plain_graph": res[("plain", "graph")][0],
-                           "tc_graph": res[("tc", "graph")][0]},
-        "speedup_vs_plain": base_ms / res[("tc", "graph")][0],
-        "speedup_vs_plain_same_loop": res[("plain", "graph")][0] / res[("tc", "graph")][0],
-        "identical_outputs": bool(np.array_equal(res[("tc", "graph")][1], base_img)
-                                  and np.array_equal(res[("plain", "graph")][1], base_img)),
+        "ms_per_removal": {"plain_engine": base_ms, "tc_engine": res[("tc", "engine")][0],
+                           "plain_graph": res[("plain", "graph")][0], "tc_graph": res[("tc", "graph")][0]},
+        "speedup_vs_plain": base_ms / res[("tc", "engine")][0],
+        "speedup_vs_plain_graph_loop": res[("plain", "graph")][0] / res[("tc", "graph")][0],
+        "identical_outputs": bool(all(np.array_equal(v[1], base_img) for v in res.values())),
         "search_kernel_us": {"plain": 1e3 * s_plain, "tc": 1e3 * s_tc},
         "search_speedup": s_plain / s_tc,
         "search_same_key": bool(k_plain == k_tc),
         "search_evals": ev,
     })
-    # algorithmic tensor work of one search: per evaluation 3 colour products
-    # for the cross term and 2 byte planes of the squared source norm (BF16
-    # in, FP32 accumulate); 3 weight sets x 3 channels = 9 MACs is the
-    # im2col count of an INT8 form
+    # the stand-alone (graph-loop) search kernel: 5 useful MACs per evaluation
     peak = peaks.get("bf16_tflops")
     ach = ev * 5 * 2 / (s_tc * 1e-3) / 1e12
-    out["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                       "frac": (ach / peak) if peak else None, "traffic": None,
-                       "peak_source": "measured bf16 burst" if peak else None,
-                       "frac_at_9_macs_per_eval": (ach * 9 / 5 / peak) if peak else None}
+    out["search_kernel_roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": (ach / peak) if peak else None, "traffic": None,
+                                     "peak_source": "measured bf16 burst" if peak else None,
+                                     "frac_at_9_macs_per_eval": (ach * 9 / 5 / peak) if peak else None}
     return out
 
 
@@ -664,7 +714,7 @@ def main():
     dev_rgb = torch.from_numpy(case.rgb).cuda()
     dev_mask = torch.from_numpy(case.mask).cuda()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # 512 MB > L2
-    ip = api.Inpainter(case.rgb, case.mask, case.r)
+    ip = api.Inpainter(case.rgb, case.mask, case.r, form=args.form, loop="engine")
     stream = ip.stream
     torch.cuda.synchronize()
 
@@ -698,33 +748,55 @@ def main():
         torch.distributed.barrier()
     total_ms = max_over_ranks(sum(ms))
     value = evals_per_removal * args.steps * world / (total_ms / 1e3)
-    plain_out = ip.result()
+    head_out = ip.result()
     search_ns, update_ns, timed_iters = ip.loop_timing()
+    tc_rounds = ip.tc_rounds()
     e2e_ms = max_over_ranks(e2e_removals(ip, case, args.steps, args.warmup))
     e2e_value = evals_per_removal * world / (e2e_ms / 1e3)
     ip.close()
     clocks = clk.summary()
+    # the other form on the same removal (same timing rules, fewer steps)
+    other = "plain" if args.form == "tc" else "tc"
+    with api.Inpainter(case.rgb, case.mask, case.r, form=other, loop="engine") as ip2:
+        o_tot, o_run, _ = time_removals(ip2, dev_rgb, dev_mask, max(3, args.steps // 2), 2, flush)
+        o_s, o_u, o_it = ip2.loop_timing()
+        other_out = ip2.result()
 
     line = None
     if rank == 0:
-        traffic = engine_traffic()
-        roof = roofline_plain(evals_per_removal, statistics.mean(run_ms), sms, mhz, probe, traffic)
+        if args.form == "tc":
+            roof = roofline_tc(evals_per_removal, iters, W, H, case.r, statistics.mean(run_ms), peaks,
+                               engine_traffic(ENGINE_TC_PROFILE))
+            plain_ms, plain_run, p_s, p_u, p_it = o_tot, o_run, o_s, o_u, o_it
+        else:
+            roof = roofline_plain(evals_per_removal, statistics.mean(run_ms), sms, mhz, probe, engine_traffic())
+            plain_ms, plain_run, p_s, p_u, p_it = total_ms / args.steps, statistics.mean(run_ms), search_ns, update_ns, timed_iters
         roof.update({"kernel": "k_engine (one persistent launch per removal)",
                      "phases_us_per_iteration": {"search": search_ns / 1e3 / max(timed_iters, 1),
                                                  "update": update_ns / 1e3 / max(timed_iters, 1)}})
+        plain_roof = roofline_plain(evals_per_removal, plain_run, sms, mhz, probe, engine_traffic())
+        plain_roof["phases_us_per_iteration"] = {"search": p_s / 1e3 / max(p_it, 1), "update": p_u / 1e3 / max(p_it, 1)}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32/f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "W": W, "H": H, "r": case.r, "mask_px": int(case.mask.sum()),
-                       "iterations": iters, "evals_per_removal": evals_per_removal,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/bf16/f32/f64" if args.form == "tc" else "u8/int32/f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(form=FORM_NAMES[args.form]), "W": W, "H": H, "r": case.r,
+                       "mask_px": int(case.mask.sum()), "iterations": iters, "evals_per_removal": evals_per_removal,
+                       "form": args.form, "tc_rounds": tc_rounds,
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "ms_per_removal": total_ms / args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_removal": e2e_ms,
                     "h2d_bytes_per_step": 4 * W * H, "d2h_bytes_per_step": 3 * W * H},
-            "gpu_launches": (launches_init(H) + 1) * args.steps,
+            # per removal: the initialisation kernels, (tensor-core form) the
+            # planes, and one persistent engine launch
+            "gpu_launches": (launches_init(H) + (2 if args.form == "tc" else 1)) * args.steps,
             "roofline": roof,
             "clocks": clocks,
+            "plain_engine": {"ms_per_removal": plain_ms, "value": evals_per_removal / (plain_ms / 1e3),
+                             "unit": UNIT, "roofline": plain_roof},
+            "speedup_vs_plain": plain_ms / (total_ms / args.steps) if args.form == "tc" else 1.0,
+            "identical_outputs_vs_other_form": bool(np.array_equal(head_out, other_out)),
         }
     if not args.skip_extras:
         if world == 1:
@@ -733,9 +805,11 @@ def main():
                                         world, 0 if args.no_cpu_baseline else 150, sms, mhz)
             sec2["workload"] = WORKLOAD2
             line["walkingman"] = sec2
-            line["tc"] = tc_section(api, case2, flush, 3, peaks, sec2["ms_per_removal"], out2)
-            line["tc_hd"] = tc_section(api, case, flush, 2, peaks, line["ms_per_removal"], plain_out)
-            line["overlap"] = overlap_section(api, case2, flush, 3, line["roofline"]["peak"])
+            line["tc"] = tc_section(api, case2, flush, 3, peaks, {("plain", "engine"): (sec2["ms_per_removal"], out2)})
+            known = {(args.form, "engine"): (line["ms_per_removal"], head_out),
+                     (other, "engine"): (o_tot, other_out)}
+            line["tc_hd"] = tc_section(api, case, flush, 2, peaks, known)
+            line["overlap"] = overlap_section(api, case2, flush, 3, plain_roof["peak"])
             line["init"] = init_section(api, [case2, case], flush, 5, peaks.get("hbm_gbs"))
         bsec = batch_section(api, flush, 3, rank, world)
         ssec = serving_section(api, rank, world, args.serve_seconds)
