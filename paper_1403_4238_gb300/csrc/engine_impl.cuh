@@ -373,7 +373,7 @@ struct EngSmemTail {
   int allow;  // leader: no iteration limit, status or error stops the loop after this iteration
   int stop;
   int px, py;
-  int a2;     // tensor-core search: sum of the known target pixels' squared shifted values
+  int a2row[17];  // tensor-core search: per target row, sum of the known pixels' squared shifted values
   int tc_pref;  // tensor-core search: slots the producer prefetched for the next round
   uint8_t known[2][17 * 17];  // known flags of the last two targets (by round parity)
   ResPlan plan;               // resident mode: this CTA's units and tiles
@@ -534,10 +534,16 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
 template <int R>
 __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, const TcTiles tt, TcArea tca, int ns) {
   using GT = TcEngGeom<R>;
-  constexpr int P = GT::P, NSL = GT::NSL, TP = (P + 3) & ~3;
-  uint8_t* smem = x.smem;
+  constexpr int P = GT::P, NSL = GT::NSL;
+  // the context lives in the kernel's local memory, which misses L1 (shared
+  // memory takes nearly all of it) and is re-read after every barrier or
+  // fence: keep working copies in registers, write them back at the end
+  uint8_t* const smem = x.smem;
+  const uint32_t tmem = x.tmem;
+  uint32_t tc_rows = x.tc_rows, tc_tiles = x.tc_tiles;
+  int tc_pref = x.tc_pref, tc_nb = x.tc_nb;
+  unsigned long long* const tpart = x.tpart;
   EngSmemTail& tl = *reinterpret_cast<EngSmemTail*>(smem);
-  uint32_t* tgt = reinterpret_cast<uint32_t*>(smem + ((sizeof(EngSmemTail) + 15) & ~size_t(15)));
   const ImgState& s = tl.img;
   Ctrl* c = s.ctrl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -551,11 +557,11 @@ __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, cons
   tca.tpad = reinterpret_cast<uint16_t*>(area + GT::A_BYTES);
   tca.ring = area + GT::A_BYTES + GT::TPAD_BYTES;
   tca.bits = reinterpret_cast<uint32_t*>(tca.ring + (size_t)tca.nb * tca.slot);
-  if (x.tc_nb != tca.nb) {
+  if (tc_nb != tca.nb) {
     // the ring's phases are counted from the slot sequence number modulo the
     // slot count: a new slot count restarts them (every slot of an earlier
     // image was consumed, so no barrier has a pending phase)
-    if (x.tc_nb != 0 && tid == 0) {
+    if (tc_nb != 0 && tid == 0) {
       for (int i = 0; i < kTcRing; ++i) {
         mbar_inval(&tl.bars.tc_full[i]);
         mbar_inval(&tl.bars.tc_empty[i]);
@@ -565,8 +571,8 @@ __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, cons
     }
     fence_mbar_init();
     __syncthreads();
-    x.tc_nb = tca.nb;
-    x.tc_rows = 0;
+    tc_nb = tca.nb;
+    tc_rows = 0;
   }
   const int ntiles = tt.ntx * tt.nty;
   const int first_y = s.cy0 + kTcRows * (rank / tt.ntx), first_tx = rank % tt.ntx;  // this CTA's first tile
@@ -575,17 +581,22 @@ __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, cons
   int round = 0;
   while (!tl.stop) {
     const int px = tl.px, py = tl.py;
-    const int par = round & 1;
     const bool first = round == 0;
     int bad = 0;
     // the producer starts the first tile's rows at once, unless it
     // prefetched them while the leader was updating
-    if (x.tc_pref == 0 && warp == kEngWarps - 1 && lane == 0 &&
-        !tc_produce<R>(s, tca, tl.bars, first_tx, first_y, x.tc_rows, 0, npre, limit))
+    if (tc_pref == 0 && warp == kEngWarps - 1 && lane == 0 &&
+        !tc_produce<R>(s, tca, tl.bars, first_tx, first_y, tc_rows, 0, npre, limit))
       bad = 1;
-    if (first) tc_bits_init<R>(s, tt, tca.bits, tca.ntl, rank, ns);
-    // target patch: warp dy reads row dy (lane = dx)
-    uint8_t* kn = tl.known[par];
+    if (first) {
+      tc_bits_init<R>(s, tt, tca.bits, tca.ntl, rank, ns);
+      // the padded target table's columns outside the patch stay zero
+      for (int e = tid; e < 4 * P * GT::TW; e += kEngThreads) tca.tpad[e] = 0;
+      __syncthreads();
+    }
+    // target patch: warp dy reads row dy (lane = dx) and writes its
+    // entries of the padded target table (R' G' B' and the known flag, zero
+    // where unknown) and the row's share of A2
     for (int dy = warp; dy < P; dy += kEngWarps) {
       const int tx = px + lane - R, ty = py + dy - R;
       uint32_t w = 0;
@@ -596,39 +607,49 @@ __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, cons
         known = o == 0;
         w = known ? v : 0u;
       }
+      int sq = 0;
       if (lane < P) {
-        tgt[dy * TP + lane] = w;
-        kn[dy * P + lane] = (uint8_t)known;
+        const int d0 = known ? (int)(w & 255u) - 128 : 0, d1 = known ? (int)((w >> 8) & 255u) - 128 : 0,
+                  d2 = known ? (int)((w >> 16) & 255u) - 128 : 0;
+        sq = d0 * d0 + d1 * d1 + d2 * d2;
+        uint16_t* tp = tca.tpad + dy * GT::TW + 8 + lane;
+        tp[0] = (uint16_t)bf16_of_int(d0);
+        tp[P * GT::TW] = (uint16_t)bf16_of_int(d1);
+        tp[2 * P * GT::TW] = (uint16_t)bf16_of_int(d2);
+        tp[3 * P * GT::TW] = (uint16_t)bf16_of_int(known ? 1 : 0);
       }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) tl.a2row[dy] = sq;
     }
-    __syncthreads();
-    tc_target<R>(tca.tpad, tgt, TP, kn, &tl.a2);
     __syncthreads();
     // every warp but the producer's (its copies are in flight) writes A
     tc_build_a<R>(tca.a, tca.tpad, first, 32 * (kEngWarps - 1));
     __syncthreads();
-    const int a2 = tl.a2;
+    int a2 = 0;
+#pragma unroll
+    for (int dy = 0; dy < P; ++dy) a2 += tl.a2row[dy];
     unsigned long long best = ~0ull;
     for (int kt = 0; kt < tca.ntl; ++kt) {
       const int t = rank + kt * ns;
       if (t >= ntiles) break;  // uniform
       const int y0 = s.cy0 + kTcRows * (t / tt.ntx), xs = tt.xs0 + 8 * tt.N * (t % tt.ntx);
-      const uint32_t g0 = x.tc_rows;
+      const uint32_t g0 = tc_rows;
       if (warp == kEngWarps - 1) {
         if (lane == 0 && !tc_produce<R>(s, tca, tl.bars, t % tt.ntx, y0, g0, kt == 0 ? npre : 0, NSL, limit))
           bad = 1;
         __syncwarp();
       } else if (warp == kEngWarps - 2) {
-        if (!(tt.N == 128 ? tc_issue<R, 0, 128>(tca, tl.bars, x.tmem, g0, limit)
-                          : tc_issue<R, 0, 64>(tca, tl.bars, x.tmem, g0, limit)))
+        if (!(tt.N == 128 ? tc_issue<R, 0, 128>(tca, tl.bars, tmem, g0, limit)
+                          : tc_issue<R, 0, 64>(tca, tl.bars, tmem, g0, limit)))
           bad = 1;
         // the one warp that waits for the tile's MMAs (the others sleep at
         // the block barrier: spinning warps would take issue slots from the
         // issuers)
-        if (!mbar_wait(&tl.bars.tc_done, x.tc_tiles & 1u, limit)) bad = 1;
+        if (!mbar_wait(&tl.bars.tc_done, tc_tiles & 1u, limit)) bad = 1;
       } else if (warp == kEngWarps - 3) {
-        if (!(tt.N == 128 ? tc_issue<R, 1, 128>(tca, tl.bars, x.tmem, g0, limit)
-                          : tc_issue<R, 1, 64>(tca, tl.bars, x.tmem, g0, limit)))
+        if (!(tt.N == 128 ? tc_issue<R, 1, 128>(tca, tl.bars, tmem, g0, limit)
+                          : tc_issue<R, 1, 64>(tca, tl.bars, tmem, g0, limit)))
           bad = 1;
       } else if (kt == 0 && !first) {
         // validity bits near the previous fill: needed only by the read-back
@@ -637,17 +658,17 @@ __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, cons
       tc_fence_before();
       if (__syncthreads_or(bad)) break;
       tc_fence_after();
-      best = tc_epilogue<R>(s, x.tmem, tt.N, a2, tca.bits + kt * tc_bit_words(tt.N), y0, xs, best);
+      best = tc_epilogue<R>(s, tmem, tt.N, a2, tca.bits + kt * tc_bit_words(tt.N), y0, xs, best);
       tc_fence_before();
-      ++x.tc_tiles;
-      x.tc_rows += NSL;
+      ++tc_tiles;
+      tc_rows += NSL;
       __syncthreads();  // the accumulators are read before the next tile's MMAs
     }
-    x.tc_pref = 0;
+    tc_pref = 0;
     best = block_min_u64(best, tl.red64);
     ++round;
     if (bad && tid == 0) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
-    if (tid == 0 && rank + 1 != ea.withhold) st_release64(&x.tpart[rank], key_tag(best, epoch));
+    if (tid == 0 && rank + 1 != ea.withhold) st_release64(&tpart[rank], key_tag(best, epoch));
     if (rank == 0 && tid == 0) atomicAdd(&c->tc_rounds, 1);
     if (warp == kEngWarps - 1 && lane == 0) {
       // once the leader has written this round's fill, the next round's
@@ -659,7 +680,7 @@ __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, cons
         if ((int)(ld_acquire(&tc->copied) - (epoch + 1u)) >= 0) {
           asm volatile("fence.proxy.async.global;" ::: "memory");
           n = npre;
-          if (!tc_produce<R>(s, tca, tl.bars, first_tx, first_y, x.tc_rows, 0, n, limit))
+          if (!tc_produce<R>(s, tca, tl.bars, first_tx, first_y, tc_rows, 0, n, limit))
             atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
           break;
         }
@@ -678,26 +699,30 @@ __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, cons
     prev_px = px;
     prev_py = py;
     __syncthreads();
-    x.tc_pref = tl.tc_pref;
+    tc_pref = tl.tc_pref;
     if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
   }
-  if (x.tc_pref > 0) {
+  if (tc_pref > 0) {
     // the loop stopped with a prefetch in flight: let it land and release
     // its slots (two arrivals stand for the two issuers' commits)
     if (warp == kEngWarps - 1 && lane == 0) {
-      for (int h = 0; h < x.tc_pref; ++h) {
-        const uint32_t g = x.tc_rows + (uint32_t)h;
+      for (int h = 0; h < tc_pref; ++h) {
+        const uint32_t g = tc_rows + (uint32_t)h;
         const int slot = (int)(g % (uint32_t)tca.nb);
         if (!mbar_wait(&tl.bars.tc_full[slot], (g / tca.nb) & 1u, limit)) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
         mbar_arrive(&tl.bars.tc_empty[slot]);
         mbar_arrive(&tl.bars.tc_empty[slot]);
       }
     }
-    x.tc_rows += (uint32_t)x.tc_pref;
-    x.tc_pref = 0;
+    tc_rows += (uint32_t)tc_pref;
+    tc_pref = 0;
     __syncthreads();
   }
   x.epoch = epoch;
+  x.tc_rows = tc_rows;
+  x.tc_tiles = tc_tiles;
+  x.tc_pref = tc_pref;
+  x.tc_nb = tc_nb;
 }
 
 // The loop of a leader that does not search, compiled as a function of its
@@ -724,6 +749,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   const int rank = x.rank, tsize = x.tsize;
   TeamCtl* tc = x.tc;
   unsigned long long* tpart = x.tpart;
+  const unsigned long long t_start = x.t_start;  // (the context is in local memory)
   const unsigned long long limit = ea.wait_limit_ns;
   uint32_t ph0 = x.ph0, ph1 = x.ph1;
   unsigned epoch = x.epoch;
@@ -1006,7 +1032,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     bool stop = true, ok = false;
     int npx = 0, npy = 0;
     unsigned long long t_b = 0ull;
-    EarlySel es{early_sel ? &tc->pub : nullptr, epoch, tl.allow != 0, ea.tick_ns, x.t_start, &tc->expired,
+    EarlySel es{early_sel ? &tc->pub : nullptr, epoch, tl.allow != 0, ea.tick_ns, t_start, &tc->expired,
                 kPubThread, false};
     if (tl.flag) {
       t_b = globaltimer();
@@ -1024,7 +1050,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
         if (tid == 0) {
           bool st = usm.remaining <= 0 || usm.next_key == 0ull || usm.it + 1 >= lim || status != 0 ||
                     err != 0;
-          if (!st && ea.tick_ns && globaltimer() - x.t_start > ea.tick_ns) {
+          if (!st && ea.tick_ns && globaltimer() - t_start > ea.tick_ns) {
             st = true;  // the launch's time budget is spent: resume in the next launch
             tc->expired = 1u;
           }

@@ -77,6 +77,9 @@ __host__ __device__ inline int tc_slot(int N, int r) { return (kTcRps * 5 * tc_l
 __host__ __device__ inline int tc_bit_words(int N) { return kTcRows * N / 4; }
 
 // Where a tensor-core search keeps its state: A | padded target | ring | bits.
+// The padded target table (written by the searcher's target staging):
+// tpad[(p * P + k) * TW + 8 + jj] = w_p(k, jj) for p < 4 (R' G' B', the
+// known flag) and jj in [-8, 24), zero outside the patch or where unknown.
 struct TcArea {
   uint8_t* a;
   uint16_t* tpad;
@@ -127,34 +130,6 @@ __device__ __forceinline__ void tc_bits_refresh(const ImgState& s, const TcTiles
     if (__ldcg(&s.count[(size_t)qy * s.pitch + qx]) != 0) continue;
     const int kt = t / ns, i = (qy - s.cy0) % kTcRows, x = xl % (8 * tt.N);
     atomicOr(&bits[(kt * kTcRows + i) * bw + (x >> 5)], 1u << (x & 31));
-  }
-}
-
-// Padded target table (whole block): tpad[(p * P + k) * TW + 8 + jj] = w_p(k, jj)
-// (p < 4) for jj in [-8, 24), zero outside the patch or where unknown (tgt: staged
-// words, row pitch tp, zero where unknown; known: P x P flags); and A2 (warp
-// 0 writes *a2).
-template <int R>
-__device__ __forceinline__ void tc_target(uint16_t* tpad, const uint32_t* tgt, int tp, const uint8_t* known, int* a2) {
-  using G = TcEngGeom<R>;
-  constexpr int P = G::P, TW = G::TW;
-  for (int e = threadIdx.x; e < 4 * P * TW; e += blockDim.x) {
-    const int jj = e % TW - 8, pk = e / TW, p = pk / P, k = pk - p * P;
-    int v = 0;
-    if (jj >= 0 && jj < P && known[k * P + jj]) v = p < 3 ? (int)((tgt[k * tp + jj] >> (8 * p)) & 255u) - 128 : 1;
-    tpad[e] = (uint16_t)bf16_of_int(v);
-  }
-  if (threadIdx.x < 32) {
-    int acc = 0;
-    for (int i = threadIdx.x; i < P * P; i += 32) {
-      if (!known[i]) continue;
-      const uint32_t t = tgt[(i / P) * tp + i % P];
-      const int d0 = (int)(t & 255u) - 128, d1 = (int)((t >> 8) & 255u) - 128, d2 = (int)((t >> 16) & 255u) - 128;
-      acc += d0 * d0 + d1 * d1 + d2 * d2;
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) *a2 = acc;
   }
 }
 

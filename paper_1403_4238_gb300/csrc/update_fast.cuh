@@ -471,6 +471,58 @@ __device__ void best_outside_window(const ImgState& s, UpdSmem<R>& sm, const Upd
   }
 }
 
+// best_outside_window for the threads [g0, blockDim.x) only (g0 a multiple
+// of 32, the group synchronised by named barrier 1): the speculative
+// phase's spare warps run it while the other warps' FP64 chains go on.
+// Writes sm.out_key / sm.out_idx; a block barrier must follow before they
+// are read.
+template <int R>
+__device__ void best_outside_window_group(const ImgState& s, UpdSmem<R>& sm, const UpdCache<R>& ca, int px,
+                                          int py, int g0) {
+  constexpr int R2 = UpdGeom<R>::R2;
+  const int W = s.W;
+  const int nt = (int)blockDim.x - g0, t0 = (int)threadIdx.x - g0;
+  // the group's cache loads (update_prefetch) are complete and visible
+  asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+  unsigned long long k = 0ull;
+  int idx = 0x7fffffff;
+  const int n1 = s.t1x * s.t1y;
+  for (int e = t0; e < n1; e += nt) {
+    const int ux = e % s.t1x, uy = e / s.t1x;
+    if (ux >= ca.ux0 && ux < ca.ux0 + ca.nux && uy >= ca.uy0 && uy < ca.uy0 + ca.nuy) continue;
+    if (ca.t1n) prio_take(k, idx, ca.t1c[e].key, ca.t1c[e].idx);
+    else prio_take(k, idx, __ldcg(&s.tiles1[e].key), __ldcg(&s.tiles1[e].idx));
+  }
+  for (int e = t0; e < ca.nux * ca.nuy * kT1 * kT1; e += nt) {
+    const int u = e / (kT1 * kT1), j = e % (kT1 * kT1);
+    const int tx = (ca.ux0 + u % ca.nux) * kT1 + (j & (kT1 - 1)), ty = (ca.uy0 + u / ca.nux) * kT1 + j / kT1;
+    if (tx >= ca.tx0 && tx < ca.tx0 + ca.ntx && ty >= ca.ty0 && ty < ca.ty0 + ca.nty) continue;
+    prio_take(k, idx, ca.t0c[e].key, ca.t0c[e].idx);
+  }
+  for (int e = t0; e < ca.ntx * ca.nty * kT0 * kT0; e += nt) {
+    const int t = e / (kT0 * kT0), j = e % (kT0 * kT0);
+    const int x = (ca.tx0 + t % ca.ntx) * kT0 + (j & (kT0 - 1)), y = (ca.ty0 + t / ca.ntx) * kT0 + j / kT0;
+    if (x >= W || y >= s.H || (abs(x - px) <= R2 && abs(y - py) <= R2)) continue;
+    prio_take(k, idx, ca.tp[e], y * W + x);
+  }
+  warp_best_prio(k, idx);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, w0 = g0 >> 5, nw = (int)(blockDim.x >> 5);
+  if (lane == 0) {
+    sm.red_pb[wid].key = k;
+    sm.red_pb[wid].idx = idx;
+  }
+  asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+  if (wid == w0) {
+    unsigned long long kk = w0 + lane < nw ? sm.red_pb[w0 + lane].key : 0ull;
+    int ii = w0 + lane < nw ? sm.red_pb[w0 + lane].idx : 0x7fffffff;
+    warp_best_prio(kk, ii);
+    if (lane == 0) {
+      sm.out_key = kk;
+      sm.out_idx = ii;
+    }
+  }
+}
+
 template <int R>
 __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, bool staged,
                            bool want_outside = false) {
@@ -537,13 +589,17 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
   if ((int)(threadIdx.x >> 5) == fsat_warp) warp_fsat<R>(sm);
   update_prefetch<R>(s, ca, spare ? nchain + 32 : 0, px, py);
   stage_isophotes_part<R, false>(sm, spare ? nchain + 32 : 0);
+  // with spare warps, the best priority outside the fill's window is found
+  // by them while the chains run
+  if (want_outside && spare && (int)threadIdx.x >= nchain + 32)
+    best_outside_window_group<R>(s, sm, ca, px, py, nchain + 32);
   if (threadIdx.x == 0) {
     sm.nfront = nfront;
     sm.spec_iter = it;
     sm.spec_filled = filled;
   }
   __syncthreads();
-  if (want_outside) {
+  if (want_outside && !spare) {
     best_outside_window<R>(s, sm, ca, px, py);
     __syncthreads();
   }
