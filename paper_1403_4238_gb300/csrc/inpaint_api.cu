@@ -434,8 +434,8 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
     g_last_error = "device allocation failed";
     return fail(INPAINT_ERR_NOMEM);
   }
-  if (o.form == INPAINT_FORM_TC && o.loop_mode != INPAINT_LOOP_GRAPH) {
-    // the engine's tensor-core search reads five BF16 planes of the image
+  if (o.form == INPAINT_FORM_TC) {
+    // the tensor-core search reads five BF16 planes of the image
     const size_t np = tc_plane_layout(s);
     if (np > 0 && !alloc_n(c, s.planes, np)) {
       g_last_error = "device allocation failed";
@@ -443,10 +443,6 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
     }
   }
   if (prepare_search_plain(r) != cudaSuccess) return fail(INPAINT_ERR_CUDA);
-  if (o.form == INPAINT_FORM_TC && encode_search_tc(s, &c->tc) != cudaSuccess) {
-    g_last_error = "tensor-core search: TMA descriptor encoding failed";
-    return fail(INPAINT_ERR_CUDA);
-  }
   {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || !(s.dtab = data_term_table(dev)))
@@ -539,6 +535,7 @@ int inpaint_step(inpaint_ctx* c, inpaint_step_info* info) {
   if (c->h_ctrl->status != 0) return c->h_ctrl->status;
   if (c->h_ctrl->remaining == 0) return INPAINT_DONE;
   if ((rc = set_limit(c, INT_MAX))) return rc;
+  CK(launch_planes(c->st, c->stream));  // the image may have changed since the last call
   if ((rc = launch_iteration(c, 0))) return rc;
   if ((rc = read_ctrl(c))) return rc;
   if (c->h_ctrl->status != 0) return c->h_ctrl->status;
@@ -575,6 +572,7 @@ int inpaint_run(inpaint_ctx* c, int max_iters, int* iters_done, inpaint_step_inf
     }
   } else {
     if ((rc = build_run_graph(c))) return rc;
+    CK(launch_planes(c->st, c->stream));  // the image may have changed since the last call
     CK(cudaGraphLaunch(c->run_exec, c->stream));
   }
   if ((rc = set_limit(c, INT_MAX))) return rc;
@@ -662,10 +660,16 @@ int inpaint_time_search(inpaint_ctx* c, int form, int reps, double* ms_per_searc
   if (h.remaining <= 0 || h.px < 0) return INPAINT_DONE;
   ImgState s = c->st;
   TcPlan plan{};
+  uint16_t* tmp_planes = nullptr;  // a plain-form context has no planes: build them for the timing
   if (form == INPAINT_FORM_TC) {
     CK(prepare_search_tc(s, &plan));
-    CK(encode_search_tc(s, &plan));
     s.n_partial = plan.grid;
+    if (!s.planes && s.n_partial > 0) {
+      const size_t np = tc_plane_layout(s);
+      CK(cudaMalloc(&tmp_planes, np * sizeof(uint16_t)));
+      s.planes = tmp_planes;
+    }
+    CK(launch_planes(s, c->stream));
   } else {
     CK(prepare_search_plain(s.r));
     const dim3 g = search_plain_grid(s);
@@ -673,7 +677,10 @@ int inpaint_time_search(inpaint_ctx* c, int form, int reps, double* ms_per_searc
   }
   if (s.n_partial <= 0) return INPAINT_DONE;
   unsigned long long* part = nullptr;
-  CK(cudaMalloc(&part, sizeof(unsigned long long) * s.n_partial));
+  if (cudaError_t ea = cudaMalloc(&part, sizeof(unsigned long long) * s.n_partial)) {
+    if (tmp_planes) cudaFree(tmp_planes);
+    return cuda_fail(ea, "cudaMalloc");
+  }
   s.partial = part;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto launch = [&]() {
@@ -702,6 +709,7 @@ int inpaint_time_search(inpaint_ctx* c, int form, int reps, double* ms_per_searc
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(part);
+  if (tmp_planes) cudaFree(tmp_planes);
   CK(e);
   long long n_known = 0;
   for (int y = 0; y <= y1 - y0; ++y)

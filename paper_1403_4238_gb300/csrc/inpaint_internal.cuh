@@ -388,15 +388,13 @@ cudaError_t launch_search_plain(const ImgState& s, cudaStream_t st);
 dim3 search_plain_grid(const ImgState& s);
 // Tensor-core search (search_tc.cu), patch radius 1..8: a persistent grid over
 // tiles of 8 candidate rows; one partial key per CTA (grid partials).
+// Tensor-core search, one launch per iteration: one CTA per tile of the
+// engine's tensor-core form (reads the image's BF16 planes).
 struct TcPlan {
-  int grid = 0, nx = 0, ntiles = 0, smem = 0, tmap_rows = 0;
-  bool tmap_ready = false;
-  CUtensorMap tmap;  // RGBA words, box 256 x tmap_rows (set by encode_search_tc)
+  int grid = 0, ntiles = 0, smem = 0, nb = 0, slot = 0;
 };
 // Geometry and launch shape (needs the search rectangle, not the buffers).
 cudaError_t prepare_search_tc(const ImgState& s, TcPlan* plan);
-// TMA descriptor of s.img: call once the image buffer exists.
-cudaError_t encode_search_tc(const ImgState& s, TcPlan* plan);
 cudaError_t launch_search_tc(const ImgState& s, const TcPlan& plan, cudaStream_t st);
 cudaError_t launch_update(const ImgState& s, int do_fill, unsigned long long cond_handle,
                           int use_cond, cudaStream_t st);

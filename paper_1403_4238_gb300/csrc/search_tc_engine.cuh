@@ -103,11 +103,16 @@ __device__ __forceinline__ void tc_bits_init(const ImgState& s, const TcTiles& t
       const int qy = s.cy0 + kTcRows * (t / tt.ntx) + i;
       const int qx0 = tt.xs0 + 8 * tt.N * (t % tt.ntx) + 32 * w + R;
       if (qy <= s.cy1) {
-#pragma unroll 8
+        // all 32 loads in flight together (one L2 round trip)
+        const int32_t* row = s.count + (size_t)qy * s.pitch;
+        int cnt[32];
+#pragma unroll
         for (int k = 0; k < 32; ++k) {
           const int qx = qx0 + k;
-          if (qx >= s.cx0 && qx <= s.cx1 && __ldcg(&s.count[(size_t)qy * s.pitch + qx]) == 0) v |= 1u << k;
+          cnt[k] = (qx >= s.cx0 && qx <= s.cx1) ? __ldcg(&row[qx]) : 1;
         }
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v |= (cnt[k] == 0 ? 1u : 0u) << k;
       }
     }
     bits[e] = v;
