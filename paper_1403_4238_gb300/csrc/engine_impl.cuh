@@ -375,6 +375,7 @@ struct EngSmemTail {
   int px, py;
   int a2row[17];  // tensor-core search: per target row, sum of the known pixels' squared shifted values
   int tc_pref;  // tensor-core search: slots the producer prefetched for the next round
+  CtrlSnap snap;  // leader: the control fields its update reads, taken at the round's start
   uint8_t known[2][17 * 17];  // known flags of the last two targets (by round parity)
   ResPlan plan;               // resident mode: this CTA's units and tiles
 };
@@ -1017,13 +1018,24 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     // hides behind the phases (a stop seen here ends the loop one iteration
     // later at most)
     int lim = 0, status = 0, err = 0;
+    CtrlSnap snap{};  // nothing writes these before this round's update
     if (tid == 0) {
       lim = __ldcg(&c->iter_limit);
       status = __ldcg(&c->status);
       err = __ldcg(ea.err);
+      snap.px = __ldcg(&c->px);
+      snap.py = __ldcg(&c->py);
+      snap.conf = __ldcg(&c->conf);
+      snap.prio = __ldcg(&c->prio);
+      snap.n_cand = __ldcg(&c->n_valid);
+      snap.it = __ldcg(&c->iter);
+      snap.remaining = __ldcg(&c->remaining);
     }
     spec_phase<R>(s, usm, uca, staged, early_sel);
-    if (tid == 0) tl.allow = usm.spec_iter + 1 < lim && status == 0 && err == 0;
+    if (tid == 0) {
+      tl.allow = usm.spec_iter + 1 < lim && status == 0 && err == 0;
+      tl.snap = snap;  // (the loads have long completed; the key gather's barrier publishes it)
+    }
     if (searches) {
       const unsigned long long best = search_round(px, py);
       if (tid == 0) st_release64(&tpart[rank], key_tag(best, epoch));
@@ -1037,7 +1049,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     if (tl.flag) {
       t_b = globaltimer();
       ok = update_phase<R>(s, nullptr, 0, usm, uca, kPubThread, false, &tl.key, &es,
-                           tcmode ? &tc->copied : nullptr, epoch + 1u);  // ends with a __syncthreads
+                           tcmode ? &tc->copied : nullptr, epoch + 1u, &tl.snap);  // ends with a __syncthreads
       if (ok && es.published) {
         // the next round (or the stop) went out inside the update phase
         if (tid == 0) tl.stop = usm.early_stop;

@@ -523,6 +523,14 @@ __device__ void best_outside_window_group(const ImgState& s, UpdSmem<R>& sm, con
   }
 }
 
+// The control-block fields the update phase reads, taken early by a caller
+// that knows nothing writes them before the update (the engine's leader
+// reads them at the start of its round, so their latency is hidden).
+struct CtrlSnap {
+  int px, py, n_cand, it, remaining;
+  double conf, prio;
+};
+
 template <int R>
 __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, bool staged,
                            bool want_outside = false) {
@@ -637,18 +645,20 @@ template <int R>
 __device__ bool update_phase(const ImgState& s, const unsigned long long* partial, int n_partial,
                              UpdSmem<R>& sm, UpdCache<R>& ca, int fence_thread = -1,
                              bool overlap_counts = false, const unsigned long long* best_in = nullptr,
-                             EarlySel* es = nullptr, unsigned* copied = nullptr, unsigned copied_val = 0u) {
+                             EarlySel* es = nullptr, unsigned* copied = nullptr, unsigned copied_val = 0u,
+                             const CtrlSnap* snap = nullptr) {
   using G = UpdGeom<R>;
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW, NC = G::NC;
   Ctrl* c = s.ctrl;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int W = s.W, H = s.H;
-  const int px = __ldcg(&c->px), py = __ldcg(&c->py);
-  const double cp = __ldcg(&c->conf), pp = __ldcg(&c->prio);
   // candidates of this iteration's search: the validity-count total, or the
   // admissible ones the partial-overlap search counted
-  const int n_cand = overlap_counts ? __ldcg(&c->n_adm) : __ldcg(&c->n_valid), it = __ldcg(&c->iter);
-  int remaining = __ldcg(&c->remaining);
+  const int px = snap ? snap->px : __ldcg(&c->px), py = snap ? snap->py : __ldcg(&c->py);
+  const double cp = snap ? snap->conf : __ldcg(&c->conf), pp = snap ? snap->prio : __ldcg(&c->prio);
+  const int n_cand = snap ? snap->n_cand : overlap_counts ? __ldcg(&c->n_adm) : __ldcg(&c->n_valid);
+  const int it = snap ? snap->it : __ldcg(&c->iter);
+  int remaining = snap ? snap->remaining : __ldcg(&c->remaining);
 
   // best source key: given (already reduced, in shared memory), or the
   // minimum of the partial keys in global memory
