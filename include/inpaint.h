@@ -66,7 +66,10 @@ typedef enum {
 
 /* Device allocator hooks: lets a host framework (e.g. PyTorch's caching
  * allocator) own device memory.  Both NULL: cudaMallocAsync/cudaFreeAsync on
- * the context's stream.  alloc returns NULL on failure. */
+ * the context's stream.  alloc returns NULL on failure, else a block aligned
+ * to 256 bytes like cudaMalloc's (the kernels copy 16-byte units with
+ * asynchronous copies); a context whose allocator returns a less aligned
+ * block fails to build with INPAINT_ERR_NOMEM. */
 typedef void* (*inpaint_alloc_fn)(size_t bytes, void* stream, void* user);
 typedef void (*inpaint_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 

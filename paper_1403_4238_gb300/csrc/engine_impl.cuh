@@ -436,8 +436,16 @@ __device__ inline void st_relaxed64(unsigned long long* p, unsigned long long v)
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// The leader's publishing thread: the last one, in a warp with no level-0
-// tile to scan in most iterations, so that its fence waits off the path.
+__device__ inline unsigned long long ld_relaxed64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The leader's publishing thread: the last one.  It is the update phase's
+// fence thread: its warp has no isophote or row-maximum work there, so the
+// fence it issues after the copy waits off the path, and the same fence
+// makes its later publication of the next round a release.
 constexpr int kPubThread = kEngThreads - 1;
 
 
@@ -482,32 +490,55 @@ __device__ inline unsigned long long key_untag(unsigned long long t) {
 __device__ inline bool gather_keys(const unsigned long long* slots, int n, unsigned epoch, int* err,
                                    unsigned long long limit, unsigned long long* red,
                                    unsigned long long* out) {
-  unsigned long long best = ~0ull;
-  bool late = false;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    unsigned long long v = ld_acquire64(&slots[i]);
-    if ((v & 0xffu) != (epoch & 0x7fu)) {
-      const unsigned long long t0 = globaltimer();
-      do {
-        v = ld_acquire64(&slots[i]);
-        if (globaltimer() - t0 > limit) {
+  // a key is a message of its own (the leader reads nothing else the
+  // searchers write), so relaxed loads suffice; warp 0 polls up to eight
+  // slots per lane at a time and reduces them, the other warps wait at the
+  // one barrier
+  if (threadIdx.x < 32) {
+    constexpr int U = 8;
+    const int lane = threadIdx.x;
+    const unsigned tag = epoch & 0x7fu;
+    unsigned long long best = ~0ull;
+    bool late = false;
+    const unsigned long long t0 = globaltimer();
+    for (int b = 0; b < n && !late; b += 32 * U) {
+      unsigned pending = 0u;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (b + lane + 32 * u < n) pending |= 1u << u;
+      while (pending) {
+        unsigned long long v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = (pending >> u) & 1u ? ld_relaxed64(&slots[b + lane + 32 * u]) : 0ull;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (((pending >> u) & 1u) && (v[u] & 0xffu) == tag) {
+            const unsigned long long k = key_untag(v[u]);
+            best = k < best ? k : best;
+            pending &= ~(1u << u);
+          }
+        if (pending && globaltimer() - t0 > limit) {
           late = true;
           break;
         }
-      } while ((v & 0xffu) != (epoch & 0x7fu));
+      }
     }
-    if (!late) {
-      const unsigned long long k = key_untag(v);
-      best = k < best ? k : best;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      best = ob < best ? ob : best;
+    }
+    late = __any_sync(0xffffffffu, late);
+    if (lane == 0) {
+      red[0] = late ? 1ull : 0ull;
+      *out = best;
     }
   }
-  if (__syncthreads_or(late)) {
+  __syncthreads();
+  if (red[0] != 0ull) {
     if (threadIdx.x == 0) atomicExch(err, INPAINT_ERR_TIMEOUT);
     return false;
   }
-  best = block_min_u64(best, red);
-  if (threadIdx.x == 0) *out = best;
-  __syncthreads();
   return true;
 }
 
@@ -669,7 +700,7 @@ __device__ __noinline__ void run_tc_search(const EngineArgs& ea, EngCtx& x, cons
     best = block_min_u64(best, tl.red64);
     ++round;
     if (bad && tid == 0) atomicExch(ea.err, INPAINT_ERR_TIMEOUT);
-    if (tid == 0 && rank + 1 != ea.withhold) st_release64(&tpart[rank], key_tag(best, epoch));
+    if (tid == 0 && rank + 1 != ea.withhold) st_relaxed64(&tpart[rank], key_tag(best, epoch));
     if (rank == 0 && tid == 0) atomicAdd(&c->tc_rounds, 1);
     if (warp == kEngWarps - 1 && lane == 0) {
       // once the leader has written this round's fill, the next round's
@@ -1038,7 +1069,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     }
     if (searches) {
       const unsigned long long best = search_round(px, py);
-      if (tid == 0) st_release64(&tpart[rank], key_tag(best, epoch));
+      if (tid == 0) st_relaxed64(&tpart[rank], key_tag(best, epoch));
     }
     tl.flag = gather_keys(tpart, ns, epoch, ea.err, limit, tl.red64, &tl.key);
     bool stop = true, ok = false;
@@ -1106,7 +1137,11 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   };
 
   if constexpr (kLeadOnly) {
+    if (tid == 0) usm.tiles_pending = 0;
+    __syncthreads();
     while (!tl.stop) lead_round(tl.px, tl.py, false);
+    // the last update's tile maxima, deferred by the early selection
+    if (usm.tiles_pending) update_tiles<R>(s, usm, uca, 0);
     x.epoch = epoch;
     return;
   }
@@ -1118,7 +1153,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     }
     if (searcher) {
       const unsigned long long best = search_round(px, py);
-      if (tid == 0 && rank + 1 != ea.withhold) st_release64(&tpart[rank], key_tag(best, epoch));
+      if (tid == 0 && rank + 1 != ea.withhold) st_relaxed64(&tpart[rank], key_tag(best, epoch));
     }
     // searchers and idle CTAs: wait for the next round
     if (tid == 0) {

@@ -84,6 +84,11 @@ struct inpaint_ctx {
     void* p = nullptr;
     if (opt.dev_alloc) {
       p = opt.dev_alloc(bytes, (void*)stream, opt.alloc_user);
+      if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {
+        // the kernels' 16-byte asynchronous copies need aligned blocks
+        if (opt.dev_free) opt.dev_free(p, bytes, (void*)stream, opt.alloc_user);
+        p = nullptr;
+      }
     } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
       p = nullptr;
     }

@@ -66,6 +66,23 @@ __device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int x, int
       : "memory");
 }
 
+// Asynchronous global -> shared copies of 4, 8 or 16 bytes (no registers;
+// `ok` false: no bytes are read and the destination is zero-filled).  A
+// thread waits for its own copies with cp_async_wait_all; a barrier then
+// makes them visible to the others.
+__device__ inline void cp_async4(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ inline void cp_async8(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(ok ? 8 : 0)
+               : "memory");
+}
+__device__ inline void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ inline unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

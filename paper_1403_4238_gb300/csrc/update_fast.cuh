@@ -90,6 +90,13 @@ struct __align__(16) UpdSmem {
   unsigned long long out_key;
   int out_idx;
   int early_stop;  // early selection: the loop stops after this iteration
+  // early selection: the tile maxima of the last update and the check of
+  // its selection are pending (run by the next speculative phase's spare
+  // warps, or by the leader before it leaves the image)
+  int tiles_pending;
+  unsigned long long pend_key;  // the published next target's key, index
+  int pend_idx;
+  int pend_rem;  // |Omega| after that update
   PrioBest red_pb[32];
 };
 
@@ -110,22 +117,82 @@ __device__ inline int normal_local(const UpdSmem<R>& sm, const ImgState& s, int 
   return ((nx + 8) << 8) | (ny + 8);
 }
 
-// C(p) of Eq. 2: the known part of Psi_p summed in row-major order, over the
-// in-image area.  Unknown and out-of-image entries hold +0.0 in sm.cf, and
-// adding +0.0 to a non-negative double leaves it unchanged, so summing every
-// entry gives exactly the sum over the known pixels.
+// C(p) of Eq. 2: the known part of each row of Psi_p summed left to right,
+// the row sums then added top to bottom, over the in-image area.  Unknown and
+// out-of-image entries hold +0.0 in sm.cf, and adding +0.0 to a non-negative
+// double leaves it unchanged, so summing every entry gives exactly the sum
+// over the known pixels.  The 2R+1 row sums are independent chains: the
+// SM's FP64 unit, not the add latency, sets the pace.
 template <int R>
 __device__ inline double conf_local(const UpdSmem<R>& sm, const ImgState& s, int lx, int ly, int x,
                                     int y) {
   constexpr int NS = UpdGeom<R>::NS;
-  double sum = 0.0;
-#pragma unroll 1
-  for (int dy = -R; dy <= R; ++dy) {
+  double row[2 * R + 1];
 #pragma unroll
-    for (int dx = -R; dx <= R; ++dx) sum = __dadd_rn(sum, sm.cf[(ly + dy) * NS + lx + dx]);
+  for (int j = 0; j <= 2 * R; ++j) {
+    const double* cf = sm.cf + (ly - R + j) * NS + lx - R;
+    double a = cf[0];  // = 0.0 + cf[0] for the non-negative entries
+#pragma unroll
+    for (int i = 1; i <= 2 * R; ++i) a = __dadd_rn(a, cf[i]);
+    row[j] = a;
   }
+  double sum = row[0];
+#pragma unroll
+  for (int j = 1; j <= 2 * R; ++j) sum = __dadd_rn(sum, row[j]);
   const int n_in = (min(x + R, s.W - 1) - max(x - R, 0) + 1) * (min(y + R, s.H - 1) - max(y - R, 0) + 1);
   return __ddiv_rn(sum, (double)n_in);
+}
+
+// C(p) of Eq. 2 for the front pixels sm.list[0, nfront) of the window
+// centred at (px, py), into sm.sC: the same sums as conf_local, laid out for
+// the SM's FP64 unit.  A dependent FP64 add takes 64 cycles on a warp, and
+// the unit accepts one warp instruction about every 19 cycles whatever the
+// number of active lanes, so the 2R+1 independent row sums of a front pixel
+// go to L lanes of one warp (lane q sums rows q, q + L, ...) and four warps
+// keep the unit busy; the pixel's first lane then adds the row sums top to
+// bottom, taking them from its L - 1 neighbours by shuffle.  Threads
+// [0, 128), 32 / L front pixels per warp and pass.  No barrier.
+template <int R, int L>
+__device__ void conf_rows(const ImgState& s, UpdSmem<R>& sm, int nfront, int px, int py) {
+  using G = UpdGeom<R>;
+  constexpr int P = G::P, NS = G::NS, NW = G::NW, R2 = G::R2, RB = G::RB;
+  constexpr int MR = (P + L - 1) / L, PPW = 32 / L;
+  const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31, q = lane % L, base = lane - q;
+  for (int k0 = 0; k0 < nfront; k0 += 4 * PPW) {
+    const int k = k0 + w * PPW + lane / L;
+    const bool on = k < nfront;
+    const int i = sm.list[on ? k : 0];
+    const int wx = i % NW - R2, wy = i / NW - R2;
+    const int lx = RB + wx, ly = RB + wy;
+    double rs[MR];
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+      const int j = q + L * m;
+      double a = 0.0;
+      if (j < P) {
+        const double* cf = sm.cf + (ly - R + j) * NS + lx - R;
+        a = cf[0];  // = 0.0 + cf[0] for the non-negative entries
+#pragma unroll
+        for (int t = 1; t < P; ++t) a = __dadd_rn(a, cf[t]);
+      }
+      rs[m] = a;
+    }
+    double sum = rs[0];  // row 0 on the pixel's first lane
+#pragma unroll
+    for (int j = 1; j < P; ++j) {
+      double v;
+      if constexpr (L == 1)
+        v = rs[j];
+      else
+        v = __shfl_sync(0xffffffffu, rs[j / L], base + j % L);
+      sum = __dadd_rn(sum, v);
+    }
+    if (on && q == 0) {
+      const int x = px + wx, y = py + wy;
+      const int n_in = (min(x + R, s.W - 1) - max(x - R, 0) + 1) * (min(y + R, s.H - 1) - max(y - R, 0) + 1);
+      sm.sC[i] = __ddiv_rn(sum, (double)n_in);
+    }
+  }
 }
 
 // Strongest precomputed isophote in Psi_p, first in row-major order.
@@ -248,11 +315,12 @@ __device__ inline void stage_isophotes(UpdSmem<R>& sm) {
 // that box (the speculative phase, before the search ends, threads
 // [first, blockDim.x)); kRing true: the box itself, from the copied pixels.
 template <int R, bool kRing>
-__device__ inline void stage_isophotes_part(UpdSmem<R>& sm, int first) {
+__device__ inline void stage_isophotes_part(UpdSmem<R>& sm, int first, int last = -1) {
   constexpr int NS = UpdGeom<R>::NS, RB = UpdGeom<R>::RB, RR = R + 1, NB = 2 * RR + 1;
   constexpr int n = kRing ? NB * NB : NS * NS;
-  if ((int)threadIdx.x < first) return;
-  for (int k = (int)threadIdx.x - first; k < n; k += (int)blockDim.x - first) {
+  if (last < 0) last = (int)blockDim.x;
+  if ((int)threadIdx.x < first || (int)threadIdx.x >= last) return;
+  for (int k = (int)threadIdx.x - first; k < n; k += last - first) {
     if (kRing) {
       isophote_at<R>(sm, RB - RR + k % NB, RB - RR + k / NB);
     } else {
@@ -316,59 +384,39 @@ __device__ void update_prefetch(const ImgState& s, UpdCache<R>& ca, int first, i
   const int nux = ux1 - ux0 + 1, nuy = uy1 - uy0 + 1;
   const int n1 = s.t1x * s.t1y;
   if ((int)threadIdx.x < first) return;
-  for (int j = threadIdx.x - first; j < NC * NC; j += blockDim.x - first) {
+  // every load is an asynchronous copy into the cache, all in flight at once
+  const int step = (int)blockDim.x - first, t0 = (int)threadIdx.x - first;
+  for (int j = t0; j < NC * NC; j += step) {
     const int x = px + j % NC - 2 * R, y = py + j / NC - 2 * R;
-    ca.cnt[j] = (x >= 0 && x < W && y >= 0 && y < H) ? __ldcg(&s.count[(size_t)y * s.pitch + x]) : 0;
+    const bool ok = x >= 0 && x < W && y >= 0 && y < H;
+    cp_async4(&ca.cnt[j], ok ? &s.count[(size_t)y * s.pitch + x] : s.count, ok);
   }
   {
-    // eight loads in flight per thread
-    constexpr int U = 8;
-    const int n = ntx * nty * kT0 * kT0, step = (int)blockDim.x - first;
-    for (int e0 = threadIdx.x - first; e0 < n; e0 += U * step) {
-      unsigned long long v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * step;
-        const int t = e / (kT0 * kT0), j = e % (kT0 * kT0);
-        const int x = (tx0 + t % ntx) * kT0 + (j & (kT0 - 1)), y = (ty0 + t / ntx) * kT0 + j / kT0;
-        v[u] = (e < n && x < W && y < H) ? __ldcg(&s.prio[(size_t)y * W + x]) : 0ull;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (e0 + u * step < n) ca.tp[e0 + u * step] = v[u];
+    const int n = ntx * nty * kT0 * kT0;
+    for (int e = t0; e < n; e += step) {
+      const int t = e / (kT0 * kT0), j = e % (kT0 * kT0);
+      const int x = (tx0 + t % ntx) * kT0 + (j & (kT0 - 1)), y = (ty0 + t / ntx) * kT0 + j / kT0;
+      const bool ok = x < W && y < H;
+      cp_async8(&ca.tp[e], ok ? &s.prio[(size_t)y * W + x] : s.prio, ok);
     }
   }
   {
-    constexpr int U = 4;
-    const int n = nux * nuy * kT1 * kT1, step = (int)blockDim.x - first;
-    for (int e0 = threadIdx.x - first; e0 < n; e0 += U * step) {
-      PrioBest b[U];
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const int e = e0 + k * step;
-        const int u = e / (kT1 * kT1), j = e % (kT1 * kT1);
-        const int tx = (ux0 + u % nux) * kT1 + (j & (kT1 - 1)), ty = (uy0 + u / nux) * kT1 + j / kT1;
-        b[k].key = 0ull;
-        b[k].idx = 0x7fffffff;
-        b[k].pad = 0;
-        if (e < n && tx < s.t0x && ty < s.t0y) {
-          b[k].key = __ldcg(&s.tiles0[ty * s.t0x + tx].key);
-          b[k].idx = __ldcg(&s.tiles0[ty * s.t0x + tx].idx);
-        }
+    const int n = nux * nuy * kT1 * kT1;
+    for (int e = t0; e < n; e += step) {
+      const int u = e / (kT1 * kT1), j = e % (kT1 * kT1);
+      const int tx = (ux0 + u % nux) * kT1 + (j & (kT1 - 1)), ty = (uy0 + u / nux) * kT1 + j / kT1;
+      if (tx < s.t0x && ty < s.t0y) {
+        cp_async16(&ca.t0c[e], &s.tiles0[ty * s.t0x + tx]);
+      } else {
+        ca.t0c[e].key = 0ull;
+        ca.t0c[e].idx = 0x7fffffff;
+        ca.t0c[e].pad = 0;
       }
-#pragma unroll
-      for (int k = 0; k < U; ++k)
-        if (e0 + k * step < n) ca.t0c[e0 + k * step] = b[k];
     }
   }
   if (n1 <= kT1Cache)
-    for (int e = threadIdx.x - first; e < n1; e += blockDim.x - first) {
-      PrioBest b;
-      b.key = __ldcg(&s.tiles1[e].key);
-      b.idx = __ldcg(&s.tiles1[e].idx);
-      b.pad = 0;
-      ca.t1c[e] = b;
-    }
+    for (int e = t0; e < n1; e += step) cp_async16(&ca.t1c[e], &s.tiles1[e]);
+  cp_async_wait_all();
   if ((int)threadIdx.x == first) {
     ca.tx0 = tx0;
     ca.ty0 = ty0;
@@ -531,6 +579,78 @@ struct CtrlSnap {
   double conf, prio;
 };
 
+// The tile maxima of the last update (level-0 tiles of its priority window
+// from the cached keys, then their level-1 tiles, in global memory and the
+// caches) and the check that the best of the tiles is the target the early
+// selection published.  Threads [g0, blockDim.x) (g0 a multiple of 32; named
+// barrier 2 when g0 > 0).  Runs before update_prefetch replaces the caches.
+template <int R>
+__device__ void update_tiles(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, int g0) {
+  const int W = s.W, nt = (int)blockDim.x - g0, t0 = (int)threadIdx.x - g0;
+  auto gsync = [&]() {
+    if (g0 == 0)
+      __syncthreads();
+    else
+      asm volatile("bar.sync 2, %0;" ::"r"(nt) : "memory");
+  };
+  const int lane = t0 & 31, wid = t0 >> 5, nw = nt >> 5;
+  for (int t = wid; t < ca.ntx * ca.nty; t += nw) {
+    const int tx = ca.tx0 + t % ca.ntx, ty = ca.ty0 + t / ca.ntx;
+    unsigned long long k = 0ull;
+    int idx = 0x7fffffff;
+#pragma unroll
+    for (int r8 = 0; r8 < kT0 * kT0 / 32; ++r8) {
+      const int j = lane + 32 * r8;
+      const int x = tx * kT0 + (j & (kT0 - 1)), y = ty * kT0 + j / kT0;
+      prio_take(k, idx, ca.tp[t * (kT0 * kT0) + j], y * W + x);
+    }
+    warp_best_prio(k, idx);
+    if (lane == 0) {
+      s.tiles0[ty * s.t0x + tx].key = k;
+      s.tiles0[ty * s.t0x + tx].idx = idx;
+      const int u = (ty / kT1 - ca.uy0) * ca.nux + (tx / kT1 - ca.ux0);
+      PrioBest& e = ca.t0c[u * (kT1 * kT1) + (ty & (kT1 - 1)) * kT1 + (tx & (kT1 - 1))];
+      e.key = k;
+      e.idx = idx;
+    }
+  }
+  gsync();
+  for (int u = wid; u < ca.nux * ca.nuy; u += nw) {
+    const int ux = ca.ux0 + u % ca.nux, uy = ca.uy0 + u / ca.nux;
+    unsigned long long k = 0ull;
+    int idx = 0x7fffffff;
+#pragma unroll
+    for (int r8 = 0; r8 < kT1 * kT1 / 32; ++r8) {
+      const PrioBest& e = ca.t0c[u * (kT1 * kT1) + lane + 32 * r8];
+      prio_take(k, idx, e.key, e.idx);
+    }
+    warp_best_prio(k, idx);
+    if (lane == 0) {
+      s.tiles1[uy * s.t1x + ux].key = k;
+      s.tiles1[uy * s.t1x + ux].idx = idx;
+      if (ca.t1n) {
+        ca.t1c[uy * s.t1x + ux].key = k;
+        ca.t1c[uy * s.t1x + ux].idx = idx;
+      }
+    }
+  }
+  gsync();
+  if (wid == 0 && sm.pend_rem > 0) {
+    unsigned long long k = 0ull;
+    int idx = 0x7fffffff;
+    if (ca.t1n) {
+      for (int j = lane; j < ca.t1n; j += 32) prio_take(k, idx, ca.t1c[j].key, ca.t1c[j].idx);
+      warp_best_prio(k, idx);
+    } else {
+      warp_global_best(s, k, idx);
+    }
+    if (lane == 0 && (k != sm.pend_key || (k != 0ull && idx != sm.pend_idx)))
+      s.ctrl->status = INPAINT_ERR_INTERNAL;  // the tiles and the early selection disagree
+  }
+  gsync();  // every read of the caches is done before they are replaced
+  if (t0 == 0) sm.tiles_pending = 0;
+}
+
 template <int R>
 __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, bool staged,
                            bool want_outside = false) {
@@ -578,29 +698,50 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
   }
   __syncthreads();
   const int nfront = sm.nlist;
-  // one long FP64 chain per front pixel, spread over the four sub-partitions;
-  // the warps the chains leave idle build the filled-flag integral image and
-  // load the update phase's cache meanwhile
-  const int nchain = (nfront + 127) & ~127;  // threads [0, nchain) run chains
-  for (int t = threadIdx.x; t < nchain; t += blockDim.x) {
-    const int k = list_entry(t);
-    if (k >= nfront) continue;
-    const int i = sm.list[k];
-    const int wx = i % NW - R2, wy = i / NW - R2;
-    const int lx = RB + wx, ly = RB + wy, x = px + wx, y = py + wy;
-    sm.sC[i] = conf_local<R>(sm, s, lx, ly, x, y);
-    sm.snrm[i] = normal_local<R>(sm, s, lx, ly, x, y);
-  }
+  // FP64 confidence sums (Eq. 2) by warps 0-3, warp 4 builds the
+  // filled-flag integral image, then both take the isophotes the fill cannot
+  // change; the other warps (the spare group) bring the tiles up to date,
+  // load the update phase's cache and find the best priority outside the
+  // fill's window
   const int nt = (int)blockDim.x;
-  const bool spare = nchain + 64 <= nt;  // at least two warps without chains
-  const int fsat_warp = spare ? nchain / 32 : 0;
-  if ((int)(threadIdx.x >> 5) == fsat_warp) warp_fsat<R>(sm);
-  update_prefetch<R>(s, ca, spare ? nchain + 32 : 0, px, py);
-  stage_isophotes_part<R, false>(sm, spare ? nchain + 32 : 0);
-  // with spare warps, the best priority outside the fill's window is found
-  // by them while the chains run
-  if (want_outside && spare && (int)threadIdx.x >= nchain + 32)
-    best_outside_window_group<R>(s, sm, ca, px, py, nchain + 32);
+  const bool spare = nt >= 256;
+  if (spare) {
+    constexpr int g0 = 160;
+    if ((int)threadIdx.x < 128) {
+      if (nfront <= 32)
+        conf_rows<R, 4>(s, sm, nfront, px, py);
+      else if (nfront <= 64)
+        conf_rows<R, 2>(s, sm, nfront, px, py);
+      else
+        conf_rows<R, 1>(s, sm, nfront, px, py);
+      for (int k = threadIdx.x; k < nfront; k += 128) {
+        const int i = sm.list[k];
+        const int wx = i % NW - R2, wy = i / NW - R2;
+        sm.snrm[i] = normal_local<R>(sm, s, RB + wx, RB + wy, px + wx, py + wy);
+      }
+    } else if ((int)threadIdx.x < g0) {
+      warp_fsat<R>(sm);
+    }
+    if ((int)threadIdx.x >= g0) {
+      if (want_outside && sm.tiles_pending) update_tiles<R>(s, sm, ca, g0);
+      update_prefetch<R>(s, ca, g0, px, py);
+      if (want_outside) best_outside_window_group<R>(s, sm, ca, px, py, g0);
+    } else {
+      stage_isophotes_part<R, false>(sm, 0, g0);
+    }
+  } else {
+    for (int k = threadIdx.x; k < nfront; k += nt) {
+      const int i = sm.list[k];
+      const int wx = i % NW - R2, wy = i / NW - R2;
+      const int lx = RB + wx, ly = RB + wy, x = px + wx, y = py + wy;
+      sm.sC[i] = conf_local<R>(sm, s, lx, ly, x, y);
+      sm.snrm[i] = normal_local<R>(sm, s, lx, ly, x, y);
+    }
+    if (threadIdx.x < 32) warp_fsat<R>(sm);
+    if (want_outside && sm.tiles_pending) update_tiles<R>(s, sm, ca, 0);
+    update_prefetch<R>(s, ca, 0, px, py);
+    stage_isophotes_part<R, false>(sm, 0);
+  }
   if (threadIdx.x == 0) {
     sm.nfront = nfront;
     sm.spec_iter = it;
@@ -687,29 +828,74 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   const int q = (int)(best & 0xffffffffull);
   const int qx = q % W, qy = q / W;
 
-  // copy the unknown in-image part of Psi_p^ from Psi_q~
-  for (int i = tid; i < P * P; i += nt) {
-    if (!sm.filled[i]) continue;
-    const int dy = i / P - R, dx = i % P - R;
-    const int l = (RB + dy) * NS + RB + dx;
-    const int tx = px + dx, ty = py + dy;
-    const uint32_t w = __ldcg(&s.img[(size_t)(qy + dy) * s.pitch + qx + dx]);
-    const uint8_t g = (uint8_t)luma_word(w);
-    const size_t t = (size_t)ty * W + tx;
-    s.img[(size_t)ty * s.pitch + tx] = w;
-    if (s.planes) plane_store(s, tx, ty, w);  // the tensor-core search's operands
-    s.gray[t] = g;
-    s.conf[t] = cp;
-    s.omega[t] = 0;
-    sm.gr[l] = g;
+  // one pass over: the copy of the unknown in-image part of Psi_p^ from
+  // Psi_q~ (first, so that its loads go out at once), the validity counts of
+  // the candidates the fill touches (they depend on the filled pixels only),
+  // and key 0 for the window's pixels off the new front; everything the next
+  // search reads is written here, before the fence below
+  const int ctx0 = ca.tx0, cty0 = ca.ty0, cntx = ca.ntx;
+  // the window's keys before this update (every key of the cached level-0
+  // tiles, from update_prefetch); a front pixel's key is never 0
+  auto cache_key = [&](int x, int y) -> unsigned long long& {
+    const int t = (y / kT0 - cty0) * cntx + (x / kT0 - ctx0);
+    return ca.tp[t * (kT0 * kT0) + (y & (kT0 - 1)) * kT0 + (x & (kT0 - 1))];
+  };
+  auto cache_prio = [&](int x, int y, unsigned long long key) { cache_key(x, y) = key; };
+  int newly = 0;
+  for (int t = tid; t < P * P + NC * NC + NW * NW; t += nt) {
+    if (t < P * P) {
+      const int i = t;
+      if (!sm.filled[i]) continue;
+      const int dy = i / P - R, dx = i % P - R;
+      const int l = (RB + dy) * NS + RB + dx;
+      const int tx = px + dx, ty = py + dy;
+      const uint32_t w = __ldcg(&s.img[(size_t)(qy + dy) * s.pitch + qx + dx]);
+      const uint8_t g = (uint8_t)luma_word(w);
+      const size_t q = (size_t)ty * W + tx;
+      s.img[(size_t)ty * s.pitch + tx] = w;
+      if (s.planes) plane_store(s, tx, ty, w);  // the tensor-core search's operands
+      s.gray[q] = g;
+      s.conf[q] = cp;
+      s.omega[q] = 0;
+      sm.gr[l] = g;
+    } else if (t < P * P + NC * NC) {
+      const int j = t - P * P;
+      const int wy = j / NC - 2 * R, wx = j % NC - 2 * R;
+      const int x = px + wx, y = py + wy;
+      if (x < 0 || x >= W || y < 0 || y >= H) continue;
+      const int u0 = max(0, wx), u1 = min(P - 1, wx + 2 * R);
+      const int v0 = max(0, wy), v1 = min(P - 1, wy + 2 * R);
+      constexpr int P1 = P + 1;
+      const int dec = sm.fsat[(v1 + 1) * P1 + u1 + 1] - sm.fsat[v0 * P1 + u1 + 1] -
+                      sm.fsat[(v1 + 1) * P1 + u0] + sm.fsat[v0 * P1 + u0];
+      if (dec) {
+        const int nv = ca.cnt[j] - dec;
+        s.count[(size_t)y * s.pitch + x] = nv;
+        if (nv == 0 && x >= s.cx0 && x <= s.cx1 && y >= s.cy0 && y <= s.cy1) ++newly;
+      }
+    } else {
+      const int i = t - P * P - NC * NC;
+      if (sm.snrm[i] != kSpecNotFront) continue;  // outside, or a front pixel
+      const int x = px + i % NW - R2, y = py + i / NW - R2;
+      unsigned long long& ck = cache_key(x, y);
+      if (ck == 0ull) continue;  // not on the old front: key and C are 0 already
+      const size_t p = (size_t)y * W + x;
+      s.prio[p] = 0ull;
+      s.pconf[p] = 0.0;
+      ck = 0ull;
+    }
   }
   __syncthreads();
-  if (copied && tid == 0) {
-    // the fill is in the image (and its planes): the searchers may prefetch
-    // the next round's source rows (the barrier above orders every thread's
-    // copy before this release)
+  const int fthread = fence_thread >= 0 ? fence_thread : copied ? 0 : -1;
+  if (tid == fthread) {
+    // every write the next search reads (pixels, planes, mask, counts) is
+    // issued; the barrier above orders the other threads' ones before this
+    // fence, which also serves the thread's later publication of the next
+    // round.  The fence thread has no isophote or row-maximum work below, so
+    // its wait overlaps them.  Then the searchers may prefetch the next
+    // round's first source rows.
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(copied), "r"(copied_val) : "memory");
+    if (copied) asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(copied), "r"(copied_val) : "memory");
   }
   const int nx_in = min(px + R, W - 1) - max(px - R, 0) + 1;
   const int ny_in = min(py + R, H - 1) - max(py - R, 0) + 1;
@@ -727,7 +913,8 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   uint32_t* hkey = reinterpret_cast<uint32_t*>(sm.cf);
   static_assert(sizeof(sm.cf) >= sizeof(uint32_t) * HR * NW, "key scratch");
   static_assert(NS * NS <= 4096, "local index fits in 12 bits");
-  for (int i = tid; i < HR * NW; i += nt) {
+  const int nhk = nt >= 512 ? nt - 32 : nt;  // the last warp (the fence thread's) sits out
+  for (int i = tid; i < HR * NW && tid < nhk; i += nhk) {
     const int ly = RB - R2 - R + i / NW, lx = RB - R2 + i % NW;
     uint32_t best = 0u;
 #pragma unroll
@@ -741,83 +928,48 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   }
   __syncthreads();
 
-  // priorities of the window (front pixels from the compact list, spread
-  // over the sub-partitions; the others get key 0) and validity counts;
-  // new keys also go to the cached level-0 tiles
-  const int ctx0 = ca.tx0, cty0 = ca.ty0, cntx = ca.ntx;
-  auto cache_prio = [&](int x, int y, unsigned long long key) {
-    const int t = (y / kT0 - cty0) * cntx + (x / kT0 - ctx0);
-    ca.tp[t * (kT0 * kT0) + (y & (kT0 - 1)) * kT0 + (x & (kT0 - 1))] = key;
-  };
-  int newly = 0;
+  // priorities of the new front (from the compact list, spread over the
+  // sub-partitions); the new keys also go to the cached level-0 tiles
   const int nlist = (nfront + 127) & ~127;
   unsigned long long wk = 0ull;  // best new key of the window (early selection)
   int wi = 0x7fffffff;
-  for (int t = tid; t < nlist + NW * NW + NC * NC; t += nt) {
-    if (t < nlist) {
-      const int k = list_entry(t);
-      if (k >= nfront) continue;
-      const int i = sm.list[k];
-      const int wx = i % NW - R2, wy = i / NW - R2;
-      int gx, gy;
-      uint32_t ik = 0u;  // column maximum of the row maxima
+  for (int t = tid; t < nlist; t += nt) {
+    const int k = list_entry(t);
+    if (k >= nfront) continue;
+    const int i = sm.list[k];
+    const int wx = i % NW - R2, wy = i / NW - R2;
+    int gx, gy;
+    uint32_t ik = 0u;  // column maximum of the row maxima
 #pragma unroll
-      for (int dy = 0; dy <= 2 * R; ++dy) {
-        const uint32_t key = hkey[(i / NW + dy) * NW + i % NW];
-        ik = key > ik ? key : ik;
-      }
-      gx = 0;
-      gy = 0;
-      if (ik) {
-        const int g = sm.gxy[4095 - (int)(ik & 4095u)];
-        gx = (g >> 16) - 512;
-        gy = (g & 0xffff) - 512;
-      }
-      const double cc = sm.sC[i];
-      const int nrm = sm.snrm[i];
-      const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
-      const int x = px + wx, y = py + wy;
-      const size_t p = (size_t)y * W + x;
-      const unsigned long long key = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
-      s.prio[p] = key;
-      s.pconf[p] = cc;
-      cache_prio(x, y, key);
-      prio_take(wk, wi, key, (int)p);
-    } else if (t < nlist + NW * NW) {
-      const int i = t - nlist;
-      if (sm.snrm[i] != kSpecNotFront) continue;  // outside, or a front pixel
-      const int x = px + i % NW - R2, y = py + i / NW - R2;
-      const size_t p = (size_t)y * W + x;
-      s.prio[p] = 0ull;
-      s.pconf[p] = 0.0;
-      cache_prio(x, y, 0ull);
-    } else {
-      const int j = t - nlist - NW * NW;
-      const int wy = j / NC - 2 * R, wx = j % NC - 2 * R;
-      const int x = px + wx, y = py + wy;
-      if (x < 0 || x >= W || y < 0 || y >= H) continue;
-      const int u0 = max(0, wx), u1 = min(P - 1, wx + 2 * R);
-      const int v0 = max(0, wy), v1 = min(P - 1, wy + 2 * R);
-      constexpr int P1 = P + 1;
-      const int dec = sm.fsat[(v1 + 1) * P1 + u1 + 1] - sm.fsat[v0 * P1 + u1 + 1] -
-                      sm.fsat[(v1 + 1) * P1 + u0] + sm.fsat[v0 * P1 + u0];
-      if (dec) {
-        const int nv = ca.cnt[j] - dec;
-        s.count[(size_t)y * s.pitch + x] = nv;
-        if (nv == 0 && x >= s.cx0 && x <= s.cx1 && y >= s.cy0 && y <= s.cy1) ++newly;
-      }
+    for (int dy = 0; dy <= 2 * R; ++dy) {
+      const uint32_t key = hkey[(i / NW + dy) * NW + i % NW];
+      ik = key > ik ? key : ik;
     }
+    gx = 0;
+    gy = 0;
+    if (ik) {
+      const int g = sm.gxy[4095 - (int)(ik & 4095u)];
+      gx = (g >> 16) - 512;
+      gy = (g & 0xffff) - 512;
+    }
+    const double cc = sm.sC[i];
+    const int nrm = sm.snrm[i];
+    const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
+    const int x = px + wx, y = py + wy;
+    const size_t p = (size_t)y * W + x;
+    const unsigned long long key = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
+    s.prio[p] = key;
+    s.pconf[p] = cc;
+    cache_prio(x, y, key);
+    prio_take(wk, wi, key, (int)p);
   }
   newly = block_sum_int(newly, sm.red32);  // includes __syncthreads
-  // every write the next search reads (pixels, mask, validity counts) is
-  // issued: the publishing thread fences them now, while the tiles are
-  // computed, so that its publication later needs no wait of its own
-  if ((int)threadIdx.x == fence_thread) asm volatile("fence.acq_rel.gpu;" ::: "memory");
   const bool early = es && es->pub;
   if (early) {
     // the next target: the better of the window's best and the best outside
-    // it; published now (after the fence above, same thread) unless the loop
-    // stops, in which case the stop goes out
+    // it; published now unless the loop stops, in which case the stop goes
+    // out (the publishing thread is the fence thread: its fence after the
+    // copy makes this store a release of everything the search reads)
     block_best_prio(wk, wi, sm.red_pb);  // every thread gets the window's best
     prio_take(wk, wi, sm.out_key, sm.out_idx);
     if ((int)threadIdx.x == es->pub_thread) {
@@ -832,6 +984,32 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       sm.early_stop = st;
     }
     es->published = true;
+    // the outcome is known: the tile maxima and the check of this selection
+    // are left to the next speculative phase's spare warps
+    if (tid == 0) {
+      const int rem = remaining - filled;
+      sm.next_key = rem > 0 ? wk : 0ull;
+      sm.next_idx = wi;
+      sm.it = it;
+      sm.remaining = rem;
+      sm.n_filled = filled;
+      sm.n_known = n_known;
+      sm.n_cand = n_cand;
+      sm.newly = newly;
+      sm.qx = qx;
+      sm.qy = qy;
+      sm.ssd = ssd;
+      sm.px = px;
+      sm.py = py;
+      sm.pp = pp;
+      sm.cp = cp;
+      sm.pend_key = wk;
+      sm.pend_idx = wi;
+      sm.pend_rem = rem;
+      sm.tiles_pending = 1;
+    }
+    __syncthreads();
+    return true;
   }
 
   // level-0 tiles from the cached keys, then level-1, then the best
@@ -893,8 +1071,6 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
         warp_global_best(s, k, idx);
       }
     }
-    if (early && remaining > 0 && (k != wk || (k != 0ull && idx != wi)) && tid == 0)
-      c->status = INPAINT_ERR_INTERNAL;  // the tiles and the early selection disagree
     if (tid == 0) {
       sm.next_key = k;
       sm.next_idx = idx;

@@ -63,6 +63,51 @@ def test_priority_hand_derived(case):
     assert (pb, cb, db) == (p, co, do)
 
 
+def test_confidence_sum_rows_then_column_hand_derived():
+    # Eq. 2 fixes no summation order; the reading is: each patch row left to
+    # right, then the row sums top to bottom.  A 3x3 patch where the orders
+    # part: row 0 = (1, u, u), row 1 = (u, p, u), row 2 = (0, 0, 0), u = 2^-53.
+    # Rows: 1 + u is a tie and rounds to even (1), again 1; row 1 = 2u = 2^-52
+    # exactly; the column: 1 + 2^-52 is representable.  Row-major order
+    # instead absorbs every u into 1.  |Psi_p| = 9 in-image pixels.
+    u = 2.0 ** -53
+    conf = np.array([[1.0, u, u], [u, 0.0, u], [0.0, 0.0, 0.0]])
+    om = np.zeros((3, 3), np.uint8)
+    om[1, 1] = 1
+    gray = np.zeros((3, 3), np.uint8)
+    assert oracle.front(om)[1, 1] == 1
+    _, c, _ = oracle.priority(gray, conf, om, 1, 1, 1)
+    assert c == (1.0 + 2.0 ** -52) / 9.0
+    assert c != 1.0 / 9.0  # the row-major value
+    _, cb, _ = brute.priority(gray.astype(np.int64), conf, om, 1, 1, 1)
+    assert cb == c
+
+
+def test_confidence_sum_fractional_against_brute_and_bound():
+    # fractional confidences (as after fills): the oracle and the brute force
+    # agree bit for bit, and the sum is within the recursive-summation bound
+    # (n - 1) eps sum|c| of the exact sum (math.fsum), which a dropped or
+    # doubled term or a wrong index would break
+    rng = np.random.default_rng(17)
+    eps = 2.0 ** -53
+    for r in (1, 4, 6, 8):
+        H, W = 3 * r + 5, 3 * r + 7
+        for _ in range(40):
+            conf = rng.random((H, W)) ** 3
+            om = (rng.random((H, W)) < 0.35).astype(np.uint8)
+            gray = rng.integers(0, 256, (H, W)).astype(np.uint8)
+            x, y = int(rng.integers(0, W)), int(rng.integers(0, H))
+            _, c, _ = oracle.priority(gray, conf, om, r, x, y)
+            _, cb, _ = brute.priority(gray.astype(np.int64), conf, om, r, x, y)
+            assert c == cb
+            vals = [float(conf[yy, xx]) for yy in range(max(0, y - r), min(H, y + r + 1))
+                    for xx in range(max(0, x - r), min(W, x + r + 1)) if not om[yy, xx]]
+            n_in = (min(W - 1, x + r) - max(0, x - r) + 1) * (min(H - 1, y + r) - max(0, y - r) + 1)
+            exact = math.fsum(vals)
+            bound = (len(vals) + 1) * eps * exact + 1e-300
+            assert abs(c * n_in - exact) <= bound + eps * n_in * c
+
+
 def test_gray_bt601_values():
     # 0.299*255 = 76.2, 0.587*255 = 149.7, 0.114*255 = 29.1 rounded to nearest
     assert oracle.gray(255, 0, 0) == 76
