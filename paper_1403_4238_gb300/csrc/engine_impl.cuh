@@ -375,7 +375,9 @@ struct EngSmemTail {
   int px, py;
   int a2row[17];  // tensor-core search: per target row, sum of the known pixels' squared shifted values
   int tc_pref;  // tensor-core search: slots the producer prefetched for the next round
-  CtrlSnap snap;  // leader: the control fields its update reads, taken at the round's start
+  CtrlSnap snap;  // leader: the control fields its update reads (kept by the leader itself)
+  int lim, status, err;  // leader: iteration limit, status and error word (the stop decision)
+  EarlySel es;           // leader: the early selection's inputs and outcome
   uint8_t known[2][17 * 17];  // known flags of the last two targets (by round parity)
   ResPlan plan;               // resident mode: this CTA's units and tiles
 };
@@ -1045,43 +1047,39 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
   // publication of the next round, bookkeeping.  Whole block.
   auto lead_round = [&](int px, int py, bool searches) {
     const unsigned long long t_a = globaltimer();
-    // the stop decision's global inputs, read now so that their latency
-    // hides behind the phases (a stop seen here ends the loop one iteration
-    // later at most)
-    int lim = 0, status = 0, err = 0;
-    CtrlSnap snap{};  // nothing writes these before this round's update
-    if (tid == 0) {
-      lim = __ldcg(&c->iter_limit);
-      status = __ldcg(&c->status);
-      err = __ldcg(ea.err);
-      snap.px = __ldcg(&c->px);
-      snap.py = __ldcg(&c->py);
-      snap.conf = __ldcg(&c->conf);
-      snap.prio = __ldcg(&c->prio);
-      snap.n_cand = __ldcg(&c->n_valid);
-      snap.it = __ldcg(&c->iter);
-      snap.remaining = __ldcg(&c->remaining);
-    }
     spec_phase<R>(s, usm, uca, staged, early_sel);
-    if (tid == 0) {
-      tl.allow = usm.spec_iter + 1 < lim && status == 0 && err == 0;
-      tl.snap = snap;  // (the loads have long completed; the key gather's barrier publishes it)
+    if (tid == 32) {
+      // the stop decision's inputs that other CTAs may change, read by a
+      // thread outside the warp that gathers the keys; everything the update
+      // reads stays in shared memory (no local-memory state: it would miss
+      // L1, which the shared memory leaves nearly empty)
+      tl.status = __ldcg(&c->status);
+      tl.err = __ldcg(ea.err);
+      tl.allow = usm.spec_iter + 1 < tl.lim && tl.status == 0 && tl.err == 0;
+      tl.es.pub = early_sel ? &tc->pub : nullptr;
+      tl.es.epoch = epoch;
+      tl.es.allow = tl.allow != 0;
+      tl.es.tick_ns = ea.tick_ns;
+      tl.es.t_start = t_start;
+      tl.es.expired = &tc->expired;
+      tl.es.pub_thread = kPubThread;
+      tl.es.published = false;
     }
-    if (searches) {
-      const unsigned long long best = search_round(px, py);
-      if (tid == 0) st_relaxed64(&tpart[rank], key_tag(best, epoch));
+    if constexpr (!kLeadOnly) {
+      if (searches) {
+        const unsigned long long best = search_round(px, py);
+        if (tid == 0) st_relaxed64(&tpart[rank], key_tag(best, epoch));
+      }
     }
     tl.flag = gather_keys(tpart, ns, epoch, ea.err, limit, tl.red64, &tl.key);
     bool stop = true, ok = false;
     int npx = 0, npy = 0;
     unsigned long long t_b = 0ull;
-    EarlySel es{early_sel ? &tc->pub : nullptr, epoch, tl.allow != 0, ea.tick_ns, t_start, &tc->expired,
-                kPubThread, false};
     if (tl.flag) {
       t_b = globaltimer();
-      ok = update_phase<R>(s, nullptr, 0, usm, uca, kPubThread, false, &tl.key, &es,
+      ok = update_phase<R>(s, nullptr, 0, usm, uca, kPubThread, false, &tl.key, &tl.es,
                            tcmode ? &tc->copied : nullptr, epoch + 1u, &tl.snap);  // ends with a __syncthreads
-      if (ok && es.published) {
+      if (ok && tl.es.published) {
         // the next round (or the stop) went out inside the update phase
         if (tid == 0) tl.stop = usm.early_stop;
         npx = usm.next_idx % s.W;
@@ -1091,8 +1089,8 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
         // Thread 0 decides (the inputs are global and may change under
         // other threads' feet) and the barrier below shares the decision.
         if (tid == 0) {
-          bool st = usm.remaining <= 0 || usm.next_key == 0ull || usm.it + 1 >= lim || status != 0 ||
-                    err != 0;
+          bool st = usm.remaining <= 0 || usm.next_key == 0ull || usm.it + 1 >= tl.lim || tl.status != 0 ||
+                    tl.err != 0;
           if (!st && ea.tick_ns && globaltimer() - t_start > ea.tick_ns) {
             st = true;  // the launch's time budget is spent: resume in the next launch
             tc->expired = 1u;
@@ -1108,7 +1106,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     // publication: the update phase's fence (same thread) already ordered
     // every write the searchers read before this store; without an update
     // (timeout or error) the store carries its own release
-    if (tid == kPubThread && !(ok && es.published)) {
+    if (tid == kPubThread && !(ok && tl.es.published)) {
       if (ok)
         st_relaxed64(&tc->pub, pub_pack(epoch + 1u, npx, npy, stop));
       else
@@ -1120,9 +1118,9 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
       tl.py = npy;
     }
     staged = ok && !stop;
-    if (staged) stage_next<R>(s, npx, npy, usm);  // next speculative phase's input
+    if (staged) stage_next<R>(s, npx, npy, usm, &tl.snap.conf);  // next speculative phase's input
     if (ok) {
-      update_finish<R>(s, usm, staged);
+      update_finish<R>(s, usm, staged, false, &tl.snap);  // and the next round's snapshot
       if (tid == 0) {
         atomicAdd(&c->t_search, t_b - t_a);
         atomicAdd(&c->t_update, globaltimer() - t_b);
@@ -1136,6 +1134,18 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
   };
 
+  if (leader && tid == 0) {
+    // the leader's snapshot of the control block; update_finish keeps it
+    // current from here on
+    tl.snap.px = __ldcg(&c->px);
+    tl.snap.py = __ldcg(&c->py);
+    tl.snap.conf = __ldcg(&c->conf);
+    tl.snap.prio = __ldcg(&c->prio);
+    tl.snap.n_cand = __ldcg(&c->n_valid);
+    tl.snap.it = __ldcg(&c->iter);
+    tl.snap.remaining = __ldcg(&c->remaining);
+    tl.lim = __ldcg(&c->iter_limit);
+  }
   if constexpr (kLeadOnly) {
     if (tid == 0) usm.tiles_pending = 0;
     __syncthreads();

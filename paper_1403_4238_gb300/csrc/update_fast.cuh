@@ -90,6 +90,7 @@ struct __align__(16) UpdSmem {
   unsigned long long out_key;
   int out_idx;
   int early_stop;  // early selection: the loop stops after this iteration
+  int upd_ok;      // update_phase: the speculation matches the iteration
   // early selection: the tile maxima of the last update and the check of
   // its selection are pending (run by the next speculative phase's spare
   // warps, or by the leader before it leaves the image)
@@ -460,7 +461,7 @@ __device__ inline void warp_fsat(UpdSmem<R>& sm) {
 // it in the control block.  Whole block; the caller's barrier makes it
 // visible.
 template <int R>
-__device__ void stage_next(const ImgState& s, int npx, int npy, UpdSmem<R>& sm) {
+__device__ void stage_next(const ImgState& s, int npx, int npy, UpdSmem<R>& sm, double* conf_out = nullptr) {
   const int t_cp = (int)blockDim.x - 1;  // a thread with the fewest staging entries
   double ncp = 0.0;
   if ((int)threadIdx.x == t_cp) ncp = __ldcg(&s.pconf[sm.next_idx]);
@@ -471,6 +472,7 @@ __device__ void stage_next(const ImgState& s, int npx, int npy, UpdSmem<R>& sm) 
     sm.nx_it = sm.it + 1;
     sm.nx_cp = ncp;
     s.ctrl->conf = ncp;
+    if (conf_out) *conf_out = ncp;
   }
 }
 
@@ -792,14 +794,6 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
   constexpr int P = G::P, RB = G::RB, NS = G::NS, R2 = G::R2, NW = G::NW, NC = G::NC;
   Ctrl* c = s.ctrl;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int W = s.W, H = s.H;
-  // candidates of this iteration's search: the validity-count total, or the
-  // admissible ones the partial-overlap search counted
-  const int px = snap ? snap->px : __ldcg(&c->px), py = snap ? snap->py : __ldcg(&c->py);
-  const double cp = snap ? snap->conf : __ldcg(&c->conf), pp = snap ? snap->prio : __ldcg(&c->prio);
-  const int n_cand = snap ? snap->n_cand : overlap_counts ? __ldcg(&c->n_adm) : __ldcg(&c->n_valid);
-  const int it = snap ? snap->it : __ldcg(&c->iter);
-  int remaining = snap ? snap->remaining : __ldcg(&c->remaining);
 
   // best source key: given (already reduced, in shared memory), or the
   // minimum of the partial keys in global memory
@@ -818,72 +812,98 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     __syncthreads();
     return false;
   }
-  const int filled = sm.spec_filled, nfront = sm.nfront;
-  if (filled == 0 || sm.spec_iter != it) {
+  // The iteration's scalars go to shared memory once (they are also the
+  // record update_finish writes): each phase below reads the ones it needs,
+  // so that none stays in a register across the phases.  A spilled one
+  // would come back from L2, since local memory misses the L1 that the
+  // shared memory leaves nearly empty.  Candidates of this iteration's
+  // search: the validity-count total, or the admissible ones the
+  // partial-overlap search counted.
+  if (tid == 0) {
+    const int px = snap ? snap->px : __ldcg(&c->px), py = snap ? snap->py : __ldcg(&c->py);
+    const int it = snap ? snap->it : __ldcg(&c->iter);
+    const int filled = sm.spec_filled, q = (int)(best & 0xffffffffull), W = s.W, H = s.H;
+    sm.px = px;
+    sm.py = py;
+    sm.cp = snap ? snap->conf : __ldcg(&c->conf);
+    sm.pp = snap ? snap->prio : __ldcg(&c->prio);
+    sm.n_cand = snap ? snap->n_cand : overlap_counts ? __ldcg(&c->n_adm) : __ldcg(&c->n_valid);
+    sm.it = it;
+    sm.n_filled = filled;
+    sm.remaining = (snap ? snap->remaining : __ldcg(&c->remaining)) - filled;
+    sm.qx = q % W;
+    sm.qy = q / W;
+    sm.ssd = (uint32_t)(best >> 32);
+    sm.n_known = (min(px + R, W - 1) - max(px - R, 0) + 1) * (min(py + R, H - 1) - max(py - R, 0) + 1) - filled;
+    sm.newly = 0;
+    sm.upd_ok = filled != 0 && sm.spec_iter == it;
+  }
+  __syncthreads();
+  if (!sm.upd_ok) {
     if (tid == 0) c->status = INPAINT_ERR_INTERNAL;  // p^ not in Omega, or stale speculation
     __syncthreads();
     return false;
   }
-  const uint32_t ssd = (uint32_t)(best >> 32);
-  const int q = (int)(best & 0xffffffffull);
-  const int qx = q % W, qy = q / W;
+  // the window's keys before this update (every key of the cached level-0
+  // tiles, from update_prefetch); a front pixel's key is never 0
+  auto cache_key = [&](int x, int y) -> unsigned long long& {
+    const int t = (y / kT0 - ca.ty0) * ca.ntx + (x / kT0 - ca.tx0);
+    return ca.tp[t * (kT0 * kT0) + (y & (kT0 - 1)) * kT0 + (x & (kT0 - 1))];
+  };
 
   // one pass over: the copy of the unknown in-image part of Psi_p^ from
   // Psi_q~ (first, so that its loads go out at once), the validity counts of
   // the candidates the fill touches (they depend on the filled pixels only),
   // and key 0 for the window's pixels off the new front; everything the next
   // search reads is written here, before the fence below
-  const int ctx0 = ca.tx0, cty0 = ca.ty0, cntx = ca.ntx;
-  // the window's keys before this update (every key of the cached level-0
-  // tiles, from update_prefetch); a front pixel's key is never 0
-  auto cache_key = [&](int x, int y) -> unsigned long long& {
-    const int t = (y / kT0 - cty0) * cntx + (x / kT0 - ctx0);
-    return ca.tp[t * (kT0 * kT0) + (y & (kT0 - 1)) * kT0 + (x & (kT0 - 1))];
-  };
-  auto cache_prio = [&](int x, int y, unsigned long long key) { cache_key(x, y) = key; };
-  int newly = 0;
-  for (int t = tid; t < P * P + NC * NC + NW * NW; t += nt) {
-    if (t < P * P) {
-      const int i = t;
-      if (!sm.filled[i]) continue;
-      const int dy = i / P - R, dx = i % P - R;
-      const int l = (RB + dy) * NS + RB + dx;
-      const int tx = px + dx, ty = py + dy;
-      const uint32_t w = __ldcg(&s.img[(size_t)(qy + dy) * s.pitch + qx + dx]);
-      const uint8_t g = (uint8_t)luma_word(w);
-      const size_t q = (size_t)ty * W + tx;
-      s.img[(size_t)ty * s.pitch + tx] = w;
-      if (s.planes) plane_store(s, tx, ty, w);  // the tensor-core search's operands
-      s.gray[q] = g;
-      s.conf[q] = cp;
-      s.omega[q] = 0;
-      sm.gr[l] = g;
-    } else if (t < P * P + NC * NC) {
-      const int j = t - P * P;
-      const int wy = j / NC - 2 * R, wx = j % NC - 2 * R;
-      const int x = px + wx, y = py + wy;
-      if (x < 0 || x >= W || y < 0 || y >= H) continue;
-      const int u0 = max(0, wx), u1 = min(P - 1, wx + 2 * R);
-      const int v0 = max(0, wy), v1 = min(P - 1, wy + 2 * R);
-      constexpr int P1 = P + 1;
-      const int dec = sm.fsat[(v1 + 1) * P1 + u1 + 1] - sm.fsat[v0 * P1 + u1 + 1] -
-                      sm.fsat[(v1 + 1) * P1 + u0] + sm.fsat[v0 * P1 + u0];
-      if (dec) {
-        const int nv = ca.cnt[j] - dec;
-        s.count[(size_t)y * s.pitch + x] = nv;
-        if (nv == 0 && x >= s.cx0 && x <= s.cx1 && y >= s.cy0 && y <= s.cy1) ++newly;
+  {
+    const int px = sm.px, py = sm.py, qx = sm.qx, qy = sm.qy, W = s.W, H = s.H;
+    const double cp = sm.cp;
+    int newly = 0;
+    for (int t = tid; t < P * P + NC * NC + NW * NW; t += nt) {
+      if (t < P * P) {
+        const int i = t;
+        if (!sm.filled[i]) continue;
+        const int dy = i / P - R, dx = i % P - R;
+        const int l = (RB + dy) * NS + RB + dx;
+        const int tx = px + dx, ty = py + dy;
+        const uint32_t w = __ldcg(&s.img[(size_t)(qy + dy) * s.pitch + qx + dx]);
+        const uint8_t g = (uint8_t)luma_word(w);
+        const size_t q = (size_t)ty * W + tx;
+        s.img[(size_t)ty * s.pitch + tx] = w;
+        if (s.planes) plane_store(s, tx, ty, w);  // the tensor-core search's operands
+        s.gray[q] = g;
+        s.conf[q] = cp;
+        s.omega[q] = 0;
+        sm.gr[l] = g;
+      } else if (t < P * P + NC * NC) {
+        const int j = t - P * P;
+        const int wy = j / NC - 2 * R, wx = j % NC - 2 * R;
+        const int x = px + wx, y = py + wy;
+        if (x < 0 || x >= W || y < 0 || y >= H) continue;
+        const int u0 = max(0, wx), u1 = min(P - 1, wx + 2 * R);
+        const int v0 = max(0, wy), v1 = min(P - 1, wy + 2 * R);
+        constexpr int P1 = P + 1;
+        const int dec = sm.fsat[(v1 + 1) * P1 + u1 + 1] - sm.fsat[v0 * P1 + u1 + 1] -
+                        sm.fsat[(v1 + 1) * P1 + u0] + sm.fsat[v0 * P1 + u0];
+        if (dec) {
+          const int nv = ca.cnt[j] - dec;
+          s.count[(size_t)y * s.pitch + x] = nv;
+          if (nv == 0 && x >= s.cx0 && x <= s.cx1 && y >= s.cy0 && y <= s.cy1) ++newly;
+        }
+      } else {
+        const int i = t - P * P - NC * NC;
+        if (sm.snrm[i] != kSpecNotFront) continue;  // outside, or a front pixel
+        const int x = px + i % NW - R2, y = py + i / NW - R2;
+        unsigned long long& ck = cache_key(x, y);
+        if (ck == 0ull) continue;  // not on the old front: key and C are 0 already
+        const size_t p = (size_t)y * W + x;
+        s.prio[p] = 0ull;
+        s.pconf[p] = 0.0;
+        ck = 0ull;
       }
-    } else {
-      const int i = t - P * P - NC * NC;
-      if (sm.snrm[i] != kSpecNotFront) continue;  // outside, or a front pixel
-      const int x = px + i % NW - R2, y = py + i / NW - R2;
-      unsigned long long& ck = cache_key(x, y);
-      if (ck == 0ull) continue;  // not on the old front: key and C are 0 already
-      const size_t p = (size_t)y * W + x;
-      s.prio[p] = 0ull;
-      s.pconf[p] = 0.0;
-      ck = 0ull;
     }
+    if (newly) atomicAdd(&sm.newly, newly);
   }
   __syncthreads();
   const int fthread = fence_thread >= 0 ? fence_thread : copied ? 0 : -1;
@@ -897,9 +917,6 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     if (copied) asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(copied), "r"(copied_val) : "memory");
   }
-  const int nx_in = min(px + R, W - 1) - max(px - R, 0) + 1;
-  const int ny_in = min(py + R, H - 1) - max(py - R, 0) + 1;
-  const int n_known = nx_in * ny_in - filled;
 
   // isophotes of the new grey levels (the ones the fill cannot change were
   // computed by the speculative phase), then for every front pixel the
@@ -930,40 +947,42 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
 
   // priorities of the new front (from the compact list, spread over the
   // sub-partitions); the new keys also go to the cached level-0 tiles
-  const int nlist = (nfront + 127) & ~127;
   unsigned long long wk = 0ull;  // best new key of the window (early selection)
   int wi = 0x7fffffff;
-  for (int t = tid; t < nlist; t += nt) {
-    const int k = list_entry(t);
-    if (k >= nfront) continue;
-    const int i = sm.list[k];
-    const int wx = i % NW - R2, wy = i / NW - R2;
-    int gx, gy;
-    uint32_t ik = 0u;  // column maximum of the row maxima
-#pragma unroll
-    for (int dy = 0; dy <= 2 * R; ++dy) {
-      const uint32_t key = hkey[(i / NW + dy) * NW + i % NW];
-      ik = key > ik ? key : ik;
+  {
+    const int px = sm.px, py = sm.py, W = s.W, nfront = sm.nfront;
+    const int nlist = (nfront + 127) & ~127;
+    for (int t = tid; t < nlist; t += nt) {
+      const int k = list_entry(t);
+      if (k >= nfront) continue;
+      const int i = sm.list[k];
+      const int wx = i % NW - R2, wy = i / NW - R2;
+      int gx, gy;
+      uint32_t ik = 0u;  // column maximum of the row maxima
+  #pragma unroll
+      for (int dy = 0; dy <= 2 * R; ++dy) {
+        const uint32_t key = hkey[(i / NW + dy) * NW + i % NW];
+        ik = key > ik ? key : ik;
+      }
+      gx = 0;
+      gy = 0;
+      if (ik) {
+        const int g = sm.gxy[4095 - (int)(ik & 4095u)];
+        gx = (g >> 16) - 512;
+        gy = (g & 0xffff) - 512;
+      }
+      const double cc = sm.sC[i];
+      const int nrm = sm.snrm[i];
+      const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
+      const int x = px + wx, y = py + wy;
+      const size_t p = (size_t)y * W + x;
+      const unsigned long long key = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
+      s.prio[p] = key;
+      s.pconf[p] = cc;
+      cache_key(x, y) = key;
+      prio_take(wk, wi, key, (int)p);
     }
-    gx = 0;
-    gy = 0;
-    if (ik) {
-      const int g = sm.gxy[4095 - (int)(ik & 4095u)];
-      gx = (g >> 16) - 512;
-      gy = (g & 0xffff) - 512;
-    }
-    const double cc = sm.sC[i];
-    const int nrm = sm.snrm[i];
-    const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
-    const int x = px + wx, y = py + wy;
-    const size_t p = (size_t)y * W + x;
-    const unsigned long long key = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
-    s.prio[p] = key;
-    s.pconf[p] = cc;
-    cache_prio(x, y, key);
-    prio_take(wk, wi, key, (int)p);
   }
-  newly = block_sum_int(newly, sm.red32);  // includes __syncthreads
   const bool early = es && es->pub;
   if (early) {
     // the next target: the better of the window's best and the best outside
@@ -973,11 +992,12 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     block_best_prio(wk, wi, sm.red_pb);  // every thread gets the window's best
     prio_take(wk, wi, sm.out_key, sm.out_idx);
     if ((int)threadIdx.x == es->pub_thread) {
-      bool st = remaining - filled <= 0 || wk == 0ull || !es->allow;
+      bool st = sm.remaining <= 0 || wk == 0ull || !es->allow;
       if (!st && es->tick_ns && globaltimer() - es->t_start > es->tick_ns) {
         st = true;  // the launch's time budget is spent: resume in the next launch
         *es->expired = 1u;
       }
+      const int W = s.W;
       asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(es->pub),
                    "l"(pub_word(es->epoch + 1u, st ? 0 : wi % W, st ? 0 : wi / W, st))
                    : "memory");
@@ -987,22 +1007,9 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     // the outcome is known: the tile maxima and the check of this selection
     // are left to the next speculative phase's spare warps
     if (tid == 0) {
-      const int rem = remaining - filled;
+      const int rem = sm.remaining;
       sm.next_key = rem > 0 ? wk : 0ull;
       sm.next_idx = wi;
-      sm.it = it;
-      sm.remaining = rem;
-      sm.n_filled = filled;
-      sm.n_known = n_known;
-      sm.n_cand = n_cand;
-      sm.newly = newly;
-      sm.qx = qx;
-      sm.qy = qy;
-      sm.ssd = ssd;
-      sm.px = px;
-      sm.py = py;
-      sm.pp = pp;
-      sm.cp = cp;
       sm.pend_key = wk;
       sm.pend_idx = wi;
       sm.pend_rem = rem;
@@ -1011,6 +1018,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     __syncthreads();
     return true;
   }
+  __syncthreads();  // the priority loop's cache writes before the tiles read them
 
   // level-0 tiles from the cached keys, then level-1, then the best
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -1023,7 +1031,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       const int j = lane + 32 * r8;
       const int x = tx * kT0 + (j & (kT0 - 1)), y = ty * kT0 + j / kT0;
       const unsigned long long kk = ca.tp[t * (kT0 * kT0) + j];
-      const int ii = y * W + x;
+      const int ii = y * s.W + x;
       prio_take(k, idx, kk, ii);
     }
     warp_best_prio(k, idx);
@@ -1057,13 +1065,12 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     }
   }
   __syncthreads();
-  remaining -= filled;
   {
     // every warp takes the same decision: a lone warp running while the
     // others wait at the barrier was several times slower here
     unsigned long long k = 0ull;
     int idx = 0x7fffffff;
-    if (remaining > 0) {
+    if (sm.remaining > 0) {
       if (ca.t1n) {
         for (int j = lane; j < ca.t1n; j += 32) prio_take(k, idx, ca.t1c[j].key, ca.t1c[j].idx);
         warp_best_prio(k, idx);
@@ -1074,19 +1081,6 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
     if (tid == 0) {
       sm.next_key = k;
       sm.next_idx = idx;
-      sm.it = it;
-      sm.remaining = remaining;
-      sm.n_filled = filled;
-      sm.n_known = n_known;
-      sm.n_cand = n_cand;
-      sm.newly = newly;
-      sm.qx = qx;
-      sm.qy = qy;
-      sm.ssd = ssd;
-      sm.px = px;
-      sm.py = py;
-      sm.pp = pp;
-      sm.cp = cp;
     }
   }
   __syncthreads();
@@ -1101,7 +1095,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
 // Whole block; ends with a __syncthreads.
 template <int R>
 __device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm, bool cp_staged,
-                              bool overlap_counts = false) {
+                              bool overlap_counts = false, CtrlSnap* next_snap = nullptr) {
   Ctrl* c = s.ctrl;
   const bool next = sm.remaining > 0 && sm.next_key != 0ull;
   if (threadIdx.x == 0) {
@@ -1125,6 +1119,11 @@ __device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm, bool cp_s
     c->remaining = sm.remaining;
     c->iter = sm.it + 1;
     c->n_valid = sm.n_cand + sm.newly;
+    if (next_snap) {
+      next_snap->remaining = sm.remaining;
+      next_snap->it = sm.it + 1;
+      next_snap->n_cand = sm.n_cand + sm.newly;
+    }
     if (overlap_counts) c->n_adm = 0;  // the next search counts afresh
     atomicAdd(&c->evals, (unsigned long long)sm.n_cand * (unsigned long long)sm.n_known);
     if (!next) {
@@ -1135,10 +1134,20 @@ __device__ void update_finish(const ImgState& s, const UpdSmem<R>& sm, bool cp_s
   }
   if (next && (int)threadIdx.x == (blockDim.x > 32 ? 32 : 0)) {
     // the next target, from another warp (its confidence is a global read)
+    const double prio = __longlong_as_double((long long)(sm.next_key - 1ull));
     c->px = sm.next_idx % s.W;
     c->py = sm.next_idx / s.W;
-    c->prio = __longlong_as_double((long long)(sm.next_key - 1ull));
-    if (!cp_staged) c->conf = __ldcg(&s.pconf[sm.next_idx]);
+    c->prio = prio;
+    if (!cp_staged) {
+      const double conf = __ldcg(&s.pconf[sm.next_idx]);
+      c->conf = conf;
+      if (next_snap) next_snap->conf = conf;  // (staged: stage_next wrote it)
+    }
+    if (next_snap) {
+      next_snap->px = sm.next_idx % s.W;
+      next_snap->py = sm.next_idx / s.W;
+      next_snap->prio = prio;
+    }
   }
   __syncthreads();
 }
