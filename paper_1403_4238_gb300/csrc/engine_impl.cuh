@@ -1134,6 +1134,7 @@ __device__ __forceinline__ void run_image(const EngineArgs& ea, int j, EngCtx& x
     if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
   };
 
+  if (leader) stage_dterm<R>(usm);  // (the first speculative phase's barriers publish it)
   if (leader && tid == 0) {
     // the leader's snapshot of the control block; update_finish keeps it
     // current from here on
@@ -1206,6 +1207,7 @@ __global__ void __launch_bounds__(kEngThreads) k_update_fast(ImgState s, cudaGra
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
     return;
   }
+  stage_dterm<R>(usm);  // (spec_phase's barriers publish it)
   spec_phase<R>(s, usm, uca, false);
   const bool ok = update_phase<R>(s, s.partial, s.n_partial, usm, uca, -1, s.overlap != 0);
   if (ok) update_finish<R>(s, usm, false, s.overlap != 0);

@@ -448,11 +448,6 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
     }
   }
   if (prepare_search_plain(r) != cudaSuccess) return fail(INPAINT_ERR_CUDA);
-  {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || !(s.dtab = data_term_table(dev)))
-      return fail(INPAINT_ERR_CUDA);
-  }
   *out = c;
   rc = inpaint_reset(c, rgb, rgb_stride, mask, mask_stride, 0);
   if (rc < 0) {
@@ -465,32 +460,6 @@ int create_impl(const uint8_t* rgb, int W, int H, int rgb_stride, const uint8_t*
 }  // namespace
 
 void inp::set_last_error(const char* msg) { g_last_error = msg; }
-
-// Per-device table of the data term D = (dot / sqrt(nn)) / 510 (Eq. 2 with
-// alpha = 255 and the factor 2 of the central difference), evaluated with
-// the same IEEE double operations the kernels would use (sqrt and division
-// are correctly rounded on host and device alike).  Built once per device
-// and kept for the life of the process.
-const double* inp::data_term_table(int device) {
-  static std::mutex mu;
-  static std::map<int, double*> tabs;
-  std::lock_guard<std::mutex> lk(mu);
-  auto it = tabs.find(device);
-  if (it != tabs.end()) return it->second;
-  std::vector<double> h((size_t)kDTabRows * kDTabCols);
-  for (int r = 0; r < kDTabRows; ++r) {
-    const double root = std::sqrt((double)kDTabNN[r]);
-    for (int dot = 0; dot < kDTabCols; ++dot) h[(size_t)r * kDTabCols + dot] = ((double)dot / root) / 510.0;
-  }
-  double* d = nullptr;
-  if (cudaMalloc(&d, h.size() * sizeof(double)) != cudaSuccess) return nullptr;
-  if (cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaFree(d);
-    return nullptr;
-  }
-  tabs[device] = d;
-  return d;
-}
 
 extern "C" {
 

@@ -89,10 +89,10 @@ constexpr int kSpecNotFront = -1;  // in the image, not on the post-fill front
 // lanes each.
 __device__ inline int list_entry(int t) { return ((t & 31) << 2) | ((t >> 5) & 3) | ((t >> 7) << 7); }
 
-// Data-term table: D = (dot / sqrt(nn)) / 510 for every |n|^2 = nn a Sobel
-// normal of a binary mask can take (nx, ny in [-4, 4]) and dot in [0, 2040].
+// The squared lengths nn = |n|^2 a Sobel normal of a binary mask can take
+// (nx, ny in [-4, 4]) for the data term D = (dot / sqrt(nn)) / 510, dot in
+// [0, 2040], and their codes.
 constexpr int kDTabRows = 14;
-constexpr int kDTabCols = 2041;
 __host__ __device__ inline int dtab_code(int nn) {
   switch (nn) {
     case 1: return 0;
@@ -111,7 +111,24 @@ __host__ __device__ inline int dtab_code(int nn) {
     default: return 13;  // 32, the largest
   }
 }
-constexpr int kDTabNN[kDTabRows] = {1, 2, 4, 5, 8, 9, 10, 13, 16, 17, 18, 20, 25, 32};
+__host__ __device__ inline int dtab_nn(int code) {
+  switch (code) {
+    case 0: return 1;
+    case 1: return 2;
+    case 2: return 4;
+    case 3: return 5;
+    case 4: return 8;
+    case 5: return 9;
+    case 6: return 10;
+    case 7: return 13;
+    case 8: return 16;
+    case 9: return 17;
+    case 10: return 18;
+    case 11: return 20;
+    case 12: return 25;
+    default: return 32;
+  }
+}
 
 struct ImgState {
   int W, H, r;
@@ -134,7 +151,6 @@ struct ImgState {
   Ctrl* ctrl;
   inpaint_step_info* trace;
   unsigned long long* partial;  // per-CTA best search key of the iteration
-  const double* dtab;           // data-term table (device, shared by contexts)
   // tensor-core form in the persistent engine (null otherwise): five BF16
   // planes of the image, R' G' B' (byte - 128) and the square sum
   // sq = sum_c (byte_c - 128)^2 as 256 hi and lo (sq = 256 hi + lo), stored per tile column tx
@@ -383,7 +399,6 @@ cudaError_t launch_import(const ImgState& s, const uint8_t* rgb, const uint8_t* 
 int sat_chunks(int H);  // the integral image needs (W+1)(H+1) + sat_chunks(H)*W ints
 cudaError_t prepare_search_plain(int r);
 cudaError_t launch_prio_init_fast(const ImgState& s, cudaStream_t st);  // r <= 8
-const double* data_term_table(int device);  // per-device table, built on first use
 cudaError_t launch_search_plain(const ImgState& s, cudaStream_t st);
 dim3 search_plain_grid(const ImgState& s);
 // Tensor-core search (search_tc.cu), patch radius 1..8: a persistent grid over

@@ -91,6 +91,9 @@ struct __align__(16) UpdSmem {
   int out_idx;
   int early_stop;  // early selection: the loop stops after this iteration
   int upd_ok;      // update_phase: the speculation matches the iteration
+  // the data term's divisors: s = sqrt(nn) for the 14 normal lengths, their
+  // reciprocals and that of 510 (stage_dterm, once per launch)
+  double dsq[kDTabRows], dinv[kDTabRows], dinv510;
   // early selection: the tile maxima of the last update and the check of
   // its selection are pending (run by the next speculative phase's spare
   // warps, or by the leader before it leaves the image)
@@ -100,6 +103,42 @@ struct __align__(16) UpdSmem {
   int pend_rem;  // |Omega| after that update
   PrioBest red_pb[32];
 };
+
+// a / b rounded to nearest for a divisor known in advance, from y = RN(1/b):
+// q0 = RN(a y), the remainder a - q0 b exact by one FMA, then the corrected
+// quotient RN(q0 + r y) (Markstein's division, IBM J. Res. Dev. 34(1), 1990).
+// Used only where it is checked to equal RN(a / b) for every input: the data
+// term below, for all 14 normal lengths and all 2041 dot products.
+__device__ inline double div_known(double a, double b, double y) {
+  const double q0 = __dmul_rn(a, y);
+  const double r = __fma_rn(-q0, b, a);
+  return __fma_rn(r, y, q0);
+}
+
+// The data term's divisors into shared memory (threads 0-14; a barrier must
+// follow before data_term_known reads them): correctly rounded square roots
+// and reciprocals, the same values the host computes.
+template <int R>
+__device__ inline void stage_dterm(UpdSmem<R>& sm) {
+  const int t = threadIdx.x;
+  if (t < kDTabRows) {
+    const double s = __dsqrt_rn((double)dtab_nn(t));
+    sm.dsq[t] = s;
+    sm.dinv[t] = __ddiv_rn(1.0, s);
+  } else if (t == kDTabRows) {
+    sm.dinv510 = __ddiv_rn(1.0, 510.0);
+  }
+}
+
+// D of Eq. 2, the same bits as data_term_direct: fl(fl(dot / s) / 510), both
+// quotients by div_known with the staged divisors (no global load on the
+// update's path).
+template <int R>
+__device__ inline double data_term_known(const UpdSmem<R>& sm, int dot, int nn) {
+  if (nn == 0) return 0.0;
+  const int c = dtab_code(nn);
+  return div_known(div_known((double)dot, sm.dsq[c], sm.dinv[c]), 510.0, sm.dinv510);
+}
 
 // Sobel normal of the Omega indicator at local (lx, ly) = image (x, y),
 // replicated image borders, packed as (nx + 8) << 8 | (ny + 8).
@@ -239,11 +278,6 @@ __device__ inline double data_term_direct(int dot, int nn) {
   return __ddiv_rn(__ddiv_rn((double)dot, __dsqrt_rn((double)nn)), 510.0);
 }
 
-// D from the precomputed table (same bits as data_term_direct).
-__device__ inline double data_term_table(const ImgState& s, int dot, int nn) {
-  if (nn == 0) return 0.0;
-  return __ldg(&s.dtab[dtab_code(nn) * kDTabCols + dot]);
-}
 
 // Stages the NS x NS neighbourhood of (cx, cy): mask (2 outside the image),
 // optionally grey levels and confidences (+0.0 under Omega and outside).
@@ -973,7 +1007,7 @@ __device__ bool update_phase(const ImgState& s, const unsigned long long* partia
       }
       const double cc = sm.sC[i];
       const int nrm = sm.snrm[i];
-      const double d = data_term_table(s, dot_abs(gx, gy, nrm), nn_of(nrm));
+      const double d = data_term_known(sm, dot_abs(gx, gy, nrm), nn_of(nrm));
       const int x = px + wx, y = py + wy;
       const size_t p = (size_t)y * W + x;
       const unsigned long long key = (unsigned long long)__double_as_longlong(__dmul_rn(cc, d)) + 1ull;
