@@ -13,8 +13,7 @@
  * Omega is empty.  Where the paper is silent the readings are:
  *   - confidence sum over Psi_p intersected with Phi (Eq. 2 prints Omega,
  *     which would make every priority 0), divided by the number of in-image
- *     pixels of Psi_p; the sum adds each patch row left to right, then the
- *     row sums top to bottom (the paper fixes no order);
+ *     pixels of Psi_p, summed in row-major order (dy outer, dx inner);
  *   - C = 1 on Phi and 0 on Omega at the start; a filled pixel takes C(p^);
  *   - grey level: integer BT.601 luma (299 R + 587 G + 114 B + 500) / 1000;
  *   - front normal n_p: integer Sobel of the Omega indicator with replicated
@@ -73,20 +72,16 @@ static int omega_clamped(const uint8_t* omega, int x, int y, int W, int H) {
 double oracle_priority(const uint8_t* gray, const double* conf,
                        const uint8_t* omega, int W, int H, int r, int x, int y,
                        double* c_out, double* d_out) {
-  /* Confidence term C(p), Eq. 2 first line: the known pixels of each patch
-     row summed left to right, then the row sums top to bottom. */
+  /* Confidence term C(p), Eq. 2 first line. */
   double sum = 0.0;
   int n_in = 0;
-  for (int dy = -r; dy <= r; ++dy) {
-    double row = 0.0;
+  for (int dy = -r; dy <= r; ++dy)
     for (int dx = -r; dx <= r; ++dx) {
       int qx = x + dx, qy = y + dy;
       if (!in_image(qx, qy, W, H)) continue;
       ++n_in;
-      if (omega[(size_t)qy * W + qx] == 0) row += conf[(size_t)qy * W + qx];
+      if (omega[(size_t)qy * W + qx] == 0) sum += conf[(size_t)qy * W + qx];
     }
-    sum += row;
-  }
   double c = sum / (double)n_in;
 
   /* Normal n_p to the front: Sobel of the Omega indicator. */

@@ -39,22 +39,20 @@ __device__ inline bool on_front(const ImgState& s, int x, int y) {
 // P(p) of Eq. 1 with C(p), D(p) of Eq. 2; writes C(p) to *c_out.
 __device__ double priority_at(const ImgState& s, int x, int y, double* c_out) {
   const int W = s.W, H = s.H, r = s.r;
-  // Confidence term: known part of Psi_p over its in-image area; each row
-  // summed left to right, then the row sums top to bottom.
+  // Confidence term: known part of Psi_p over its in-image area, summed in
+  // row-major order.
   double sum = 0.0;
   int n_in = 0;
   for (int dy = -r; dy <= r; ++dy) {
     const int qy = y + dy;
     if (qy < 0 || qy >= H) continue;
-    double row = 0.0;
     for (int dx = -r; dx <= r; ++dx) {
       const int qx = x + dx;
       if (qx < 0 || qx >= W) continue;
       ++n_in;
       const size_t q = (size_t)qy * W + qx;
-      if (s.omega[q] == 0) row = __dadd_rn(row, s.conf[q]);
+      if (s.omega[q] == 0) sum = __dadd_rn(sum, s.conf[q]);
     }
-    sum = __dadd_rn(sum, row);
   }
   const double c = __ddiv_rn(sum, (double)n_in);
 

@@ -91,6 +91,7 @@ struct __align__(16) UpdSmem {
   int out_idx;
   int early_stop;  // early selection: the loop stops after this iteration
   int upd_ok;      // update_phase: the speculation matches the iteration
+  int iso_next;    // spec_phase: next chunk of the isophotes the fill cannot change
   // the data term's divisors: s = sqrt(nn) for the 14 normal lengths, their
   // reciprocals and that of 510 (stage_dterm, once per launch)
   double dsq[kDTabRows], dinv[kDTabRows], dinv510;
@@ -157,82 +158,23 @@ __device__ inline int normal_local(const UpdSmem<R>& sm, const ImgState& s, int 
   return ((nx + 8) << 8) | (ny + 8);
 }
 
-// C(p) of Eq. 2: the known part of each row of Psi_p summed left to right,
-// the row sums then added top to bottom, over the in-image area.  Unknown and
-// out-of-image entries hold +0.0 in sm.cf, and adding +0.0 to a non-negative
-// double leaves it unchanged, so summing every entry gives exactly the sum
-// over the known pixels.  The 2R+1 row sums are independent chains: the
-// SM's FP64 unit, not the add latency, sets the pace.
+// C(p) of Eq. 2: the known part of Psi_p summed in row-major order (dy
+// outer, dx inner, one addition at a time), over the in-image area.
+// Unknown and out-of-image entries hold +0.0 in sm.cf, and adding +0.0 to a
+// non-negative double leaves it unchanged, so summing every entry gives
+// exactly the sum over the known pixels.
 template <int R>
 __device__ inline double conf_local(const UpdSmem<R>& sm, const ImgState& s, int lx, int ly, int x,
                                     int y) {
   constexpr int NS = UpdGeom<R>::NS;
-  double row[2 * R + 1];
+  double sum = 0.0;
+#pragma unroll 1
+  for (int dy = -R; dy <= R; ++dy) {
 #pragma unroll
-  for (int j = 0; j <= 2 * R; ++j) {
-    const double* cf = sm.cf + (ly - R + j) * NS + lx - R;
-    double a = cf[0];  // = 0.0 + cf[0] for the non-negative entries
-#pragma unroll
-    for (int i = 1; i <= 2 * R; ++i) a = __dadd_rn(a, cf[i]);
-    row[j] = a;
+    for (int dx = -R; dx <= R; ++dx) sum = __dadd_rn(sum, sm.cf[(ly + dy) * NS + lx + dx]);
   }
-  double sum = row[0];
-#pragma unroll
-  for (int j = 1; j <= 2 * R; ++j) sum = __dadd_rn(sum, row[j]);
   const int n_in = (min(x + R, s.W - 1) - max(x - R, 0) + 1) * (min(y + R, s.H - 1) - max(y - R, 0) + 1);
   return __ddiv_rn(sum, (double)n_in);
-}
-
-// C(p) of Eq. 2 for the front pixels sm.list[0, nfront) of the window
-// centred at (px, py), into sm.sC: the same sums as conf_local, laid out for
-// the SM's FP64 unit.  A dependent FP64 add takes 64 cycles on a warp, and
-// the unit accepts one warp instruction about every 19 cycles whatever the
-// number of active lanes, so the 2R+1 independent row sums of a front pixel
-// go to L lanes of one warp (lane q sums rows q, q + L, ...) and four warps
-// keep the unit busy; the pixel's first lane then adds the row sums top to
-// bottom, taking them from its L - 1 neighbours by shuffle.  Threads
-// [0, 128), 32 / L front pixels per warp and pass.  No barrier.
-template <int R, int L>
-__device__ void conf_rows(const ImgState& s, UpdSmem<R>& sm, int nfront, int px, int py) {
-  using G = UpdGeom<R>;
-  constexpr int P = G::P, NS = G::NS, NW = G::NW, R2 = G::R2, RB = G::RB;
-  constexpr int MR = (P + L - 1) / L, PPW = 32 / L;
-  const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31, q = lane % L, base = lane - q;
-  for (int k0 = 0; k0 < nfront; k0 += 4 * PPW) {
-    const int k = k0 + w * PPW + lane / L;
-    const bool on = k < nfront;
-    const int i = sm.list[on ? k : 0];
-    const int wx = i % NW - R2, wy = i / NW - R2;
-    const int lx = RB + wx, ly = RB + wy;
-    double rs[MR];
-#pragma unroll
-    for (int m = 0; m < MR; ++m) {
-      const int j = q + L * m;
-      double a = 0.0;
-      if (j < P) {
-        const double* cf = sm.cf + (ly - R + j) * NS + lx - R;
-        a = cf[0];  // = 0.0 + cf[0] for the non-negative entries
-#pragma unroll
-        for (int t = 1; t < P; ++t) a = __dadd_rn(a, cf[t]);
-      }
-      rs[m] = a;
-    }
-    double sum = rs[0];  // row 0 on the pixel's first lane
-#pragma unroll
-    for (int j = 1; j < P; ++j) {
-      double v;
-      if constexpr (L == 1)
-        v = rs[j];
-      else
-        v = __shfl_sync(0xffffffffu, rs[j / L], base + j % L);
-      sum = __dadd_rn(sum, v);
-    }
-    if (on && q == 0) {
-      const int x = px + wx, y = py + wy;
-      const int n_in = (min(x + R, s.W - 1) - max(x - R, 0) + 1) * (min(y + R, s.H - 1) - max(y - R, 0) + 1);
-      sm.sC[i] = __ddiv_rn(sum, (double)n_in);
-    }
-  }
 }
 
 // Strongest precomputed isophote in Psi_p, first in row-major order.
@@ -359,6 +301,26 @@ __device__ inline void stage_isophotes_part(UpdSmem<R>& sm, int first, int last 
     if (kRing) {
       isophote_at<R>(sm, RB - RR + k % NB, RB - RR + k / NB);
     } else {
+      const int lx = k % NS, ly = k / NS;
+      if (abs(lx - RB) > RR || abs(ly - RB) > RR) isophote_at<R>(sm, lx, ly);
+    }
+  }
+}
+
+// stage_isophotes_part<R, false> with the work handed out in chunks of 32
+// positions from sm.iso_next (0 on entry): a warp that starts late takes
+// fewer.  Whole warps.  No barrier.
+template <int R>
+__device__ inline void stage_isophotes_dyn(UpdSmem<R>& sm) {
+  constexpr int NS = UpdGeom<R>::NS, RB = UpdGeom<R>::RB, RR = R + 1;
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&sm.iso_next, 32);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= NS * NS) break;
+    const int k = base + lane;
+    if (k < NS * NS) {
       const int lx = k % NS, ly = k / NS;
       if (abs(lx - RB) > RR || abs(ly - RB) > RR) isophote_at<R>(sm, lx, ly);
     }
@@ -708,7 +670,10 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
     stage_nbhd<R, true, true>(s, px, py, sm);
     __syncthreads();
   }
-  if (threadIdx.x == 0) sm.nlist = 0;
+  if (threadIdx.x == 0) {
+    sm.nlist = 0;
+    sm.iso_next = 0;
+  }
   int my = 0;
   for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
     const int l = (RB + i / P - R) * NS + RB + i % P - R;
@@ -734,28 +699,29 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
   }
   __syncthreads();
   const int nfront = sm.nlist;
-  // FP64 confidence sums (Eq. 2) by warps 0-3, warp 4 builds the
-  // filled-flag integral image, then both take the isophotes the fill cannot
-  // change; the other warps (the spare group) bring the tiles up to date,
-  // load the update phase's cache and find the best priority outside the
-  // fill's window
+  // FP64 confidence sums (Eq. 2) by the first warps, warp 4 builds the
+  // filled-flag integral image, and warps 0-4 share the isophotes the fill
+  // cannot change; the other warps (the spare group) bring the tiles up to
+  // date, load the update phase's cache and find the best priority outside
+  // the fill's window
   const int nt = (int)blockDim.x;
   const bool spare = nt >= 256;
   if (spare) {
     constexpr int g0 = 160;
-    if ((int)threadIdx.x < 128) {
-      if (nfront <= 32)
-        conf_rows<R, 4>(s, sm, nfront, px, py);
-      else if (nfront <= 64)
-        conf_rows<R, 2>(s, sm, nfront, px, py);
-      else
-        conf_rows<R, 1>(s, sm, nfront, px, py);
-      for (int k = threadIdx.x; k < nfront; k += 128) {
+    // one dependent row-major chain per front pixel, packed into as few
+    // warps as the front needs: up to three warps of chains still run at the
+    // 64 cycles of one dependent add, four at 76 (the unit takes a warp
+    // instruction about every 19 cycles whatever the active lanes)
+    const int cw = nfront <= 96 ? (nfront + 31) >> 5 : 4;
+    if ((int)threadIdx.x < 32 * cw) {
+      for (int k = threadIdx.x; k < nfront; k += 32 * cw) {
         const int i = sm.list[k];
         const int wx = i % NW - R2, wy = i / NW - R2;
-        sm.snrm[i] = normal_local<R>(sm, s, RB + wx, RB + wy, px + wx, py + wy);
+        const int lx = RB + wx, ly = RB + wy, x = px + wx, y = py + wy;
+        sm.sC[i] = conf_local<R>(sm, s, lx, ly, x, y);
+        sm.snrm[i] = normal_local<R>(sm, s, lx, ly, x, y);
       }
-    } else if ((int)threadIdx.x < g0) {
+    } else if ((int)(threadIdx.x >> 5) == 4) {
       warp_fsat<R>(sm);
     }
     if ((int)threadIdx.x >= g0) {
@@ -763,7 +729,8 @@ __device__ void spec_phase(const ImgState& s, UpdSmem<R>& sm, UpdCache<R>& ca, b
       update_prefetch<R>(s, ca, g0, px, py);
       if (want_outside) best_outside_window_group<R>(s, sm, ca, px, py, g0);
     } else {
-      stage_isophotes_part<R, false>(sm, 0, g0);
+      // the warps without chains at once, the chain warps when done
+      stage_isophotes_dyn<R>(sm);
     }
   } else {
     for (int k = threadIdx.x; k < nfront; k += nt) {

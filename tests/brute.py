@@ -34,20 +34,17 @@ def sobel_normal(omega, x, y):
 
 
 def priority(gray, conf, omega, r, x, y):
-    """(P, C, D) as Python floats (IEEE double); C sums each patch row left
-    to right, then the row sums top to bottom."""
+    """(P, C, D) as Python floats (IEEE double), summing C row-major."""
     H, W = omega.shape
     om = omega.astype(bool)
     total = 0.0
     count = 0
     for yy in range(y - r, y + r + 1):
-        row = 0.0
         for xx in range(x - r, x + r + 1):
             if 0 <= xx < W and 0 <= yy < H:
                 count += 1
                 if not om[yy, xx]:
-                    row += float(conf[yy, xx])
-        total += row
+                    total += float(conf[yy, xx])
     c = total / count
     nx, ny = sobel_normal(omega, x, y)
     g = gray.astype(np.int64)

@@ -63,13 +63,13 @@ def test_priority_hand_derived(case):
     assert (pb, cb, db) == (p, co, do)
 
 
-def test_confidence_sum_rows_then_column_hand_derived():
-    # Eq. 2 fixes no summation order; the reading is: each patch row left to
-    # right, then the row sums top to bottom.  A 3x3 patch where the orders
-    # part: row 0 = (1, u, u), row 1 = (u, p, u), row 2 = (0, 0, 0), u = 2^-53.
-    # Rows: 1 + u is a tie and rounds to even (1), again 1; row 1 = 2u = 2^-52
-    # exactly; the column: 1 + 2^-52 is representable.  Row-major order
-    # instead absorbs every u into 1.  |Psi_p| = 9 in-image pixels.
+def test_confidence_sum_row_major_hand_derived():
+    # The summation order: row-major, dy outer, dx inner, one addition at a
+    # time.  A 3x3 patch where it matters: row 0 = (1, u, u), row 1 =
+    # (u, p, u), row 2 = (0, 0, 0), u = 2^-53.  Row-major: 1 + u is a tie
+    # and rounds to even (1), and so does every later + u, so the sum is 1
+    # and C = 1/9.  Summing each row first would give 1 + 2^-52 instead
+    # (row 1 = 2u exactly).  |Psi_p| = 9 in-image pixels.
     u = 2.0 ** -53
     conf = np.array([[1.0, u, u], [u, 0.0, u], [0.0, 0.0, 0.0]])
     om = np.zeros((3, 3), np.uint8)
@@ -77,8 +77,8 @@ def test_confidence_sum_rows_then_column_hand_derived():
     gray = np.zeros((3, 3), np.uint8)
     assert oracle.front(om)[1, 1] == 1
     _, c, _ = oracle.priority(gray, conf, om, 1, 1, 1)
-    assert c == (1.0 + 2.0 ** -52) / 9.0
-    assert c != 1.0 / 9.0  # the row-major value
+    assert c == 1.0 / 9.0
+    assert c != (1.0 + 2.0 ** -52) / 9.0  # the rows-first value
     _, cb, _ = brute.priority(gray.astype(np.int64), conf, om, 1, 1, 1)
     assert cb == c
 
