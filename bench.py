@@ -215,7 +215,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(vals),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32/f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.format(form=FORM_NAMES[args.form]), "W": int(case.rgb.shape[1]),
+                   "H": int(case.rgb.shape[0]), "r": case.r, "mask_px": int(case.mask.sum()), "form": args.form,
+                   "parallelism": "one host thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
